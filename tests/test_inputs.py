@@ -1,0 +1,92 @@
+"""Seeded input generators: shapes of the paper's Si64 benchmark systems."""
+import json
+import os
+
+import numpy as np
+
+from paper_2009_03559_gb300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "si64_shell_counts.json")
+
+
+def test_si64_shell_and_function_counts():
+    """Paper Sec. 4: Si64 SZ = 128 shells / 256 functions, DZP = 320 / 832."""
+    g = json.load(open(GOLD))
+    sz = inputs.cluster_system(64, seed=1)
+    assert sz.n_atoms == g["SZ"]["atoms"]
+    assert sz.n_shells == g["SZ"]["shells"]
+    assert sz.n_bf == g["SZ"]["functions"]
+    dzp = inputs.diamond_system(64, seed=1)
+    assert dzp.n_shells == g["DZP"]["shells"]
+    assert dzp.n_bf == g["DZP"]["functions"]
+
+
+def test_config_sizes():
+    s0, p0 = inputs.config0()
+    assert (s0.n_atoms, s0.n_shells, s0.n_bf) == (16, 32, 64)
+    assert p0.shape == (64, 64)
+    s1, p1 = inputs.config1()
+    assert (s1.n_atoms, s1.n_shells, s1.n_bf) == (64, 320, 832)
+    s3 = inputs.diamond_system(216, seed=3000)
+    assert (s3.n_shells, s3.n_bf) == (1080, 2808)
+
+
+def test_diamond_geometry():
+    s = inputs.diamond_system(64, seed=5, jitter=0.0)
+    d = np.linalg.norm(s.xyz[:, None] - s.xyz[None], axis=-1)
+    d[np.diag_indices(64)] = np.inf
+    assert np.isclose(d.min(), 10.26 * np.sqrt(3) / 4)  # nearest neighbour a*sqrt(3)/4
+    # 2x2x2 conventional cells: extent a*(2 - 1/4) along each axis
+    assert np.allclose(s.xyz.max(0) - s.xyz.min(0), 10.26 * 1.75)
+
+
+def test_cluster_geometry_and_jitter():
+    s = inputs.cluster_system(16, seed=0, jitter=0.0)
+    assert np.allclose(s.xyz[:3], [[0, 0, 0], [0, 0, 2.5], [0, 0, 5.0]])
+    sj = inputs.cluster_system(16, seed=0)
+    assert np.abs(sj.xyz - s.xyz).max() <= 0.3
+
+
+def test_exponents_and_weights():
+    s = inputs.diamond_system(8, seed=3)
+    a = s.alpha.reshape(-1, 3)
+    assert np.all(np.diff(a, axis=1) <= 0)  # sorted descending within a shell
+    assert a.min() >= 0.08 and a.max() <= 8.0
+    assert s.coef.min() >= 0.1 and s.coef.max() < 1.0
+    c = inputs.cluster_system(8, seed=3)
+    assert c.alpha.min() >= 0.1 and c.alpha.max() <= 20.0
+
+
+def test_density_matrix_projector():
+    s, p = inputs.config0()
+    assert np.allclose(p, p.T)
+    assert np.allclose(p @ p, p, atol=1e-12)          # P = C C^T with orthonormal C
+    assert np.isclose(np.trace(p), 32.0)
+
+
+def test_density_truncation():
+    s, p = inputs.config1(n_atoms=16)
+    ba = s.bf_atom
+    d = np.linalg.norm(s.xyz[:, None] - s.xyz[None], axis=-1)[ba][:, ba]
+    assert np.all(p[d > 10.0] == 0.0)
+    assert np.any(p[d <= 10.0] != 0.0)
+    assert np.array_equal(p, p.T)
+
+
+def test_determinism():
+    a, pa = inputs.config0()
+    b, pb = inputs.config0()
+    assert np.array_equal(a.xyz, b.xyz) and np.array_equal(a.alpha, b.alpha)
+    assert np.array_equal(pa, pb)
+
+
+def test_batch_and_requests():
+    sys_ = inputs.config2_systems(n_systems=4)
+    assert len(sys_) == 4
+    for s, p in sys_:
+        assert 8 <= s.n_atoms <= 128 and p.shape == (s.n_bf, s.n_bf)
+    systems, reqs = inputs.config4_requests(n_requests=50)
+    assert len(systems) == 64 and len(reqs) == 50
+    times = [r[0] for r in reqs]
+    assert all(np.diff(times) > 0)
+    assert all(16 <= n <= 512 for _, n, _ in systems)
