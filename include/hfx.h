@@ -1,0 +1,169 @@
+/*
+ * hfx.h -- C ABI of the GB300 (sm_103a) screened HSE exact-exchange library.
+ *
+ * The library builds the exchange matrix of the paper's hybrid-functional method
+ * (Sec. 2, Eq. vx, for one cell and without lattice images or the -1/2 prefactor):
+ *
+ *     K_{mu nu} = sum_{lambda sigma} (mu lambda | nu sigma)_omega P_{lambda sigma}
+ *
+ * over contracted Gaussian shells of angular momentum 0..2 with (2l+1) spherical
+ * functions each (Sec. 3.1, shell quartets; Cartesian -> spherical step, Sec. 3.1),
+ * with the HSE06 short-range kernel erfc(omega r)/r in the two-electron integral
+ * (Sec. 2, ERI definition; Sec. 4, HSE06).  A shell quartet (IJ|KL) contributes iff
+ * pair IJ and pair KL are kept and Q_IJ Q_KL >= tau (Schwarz screening, Sec. 3.1
+ * Eq. schwarz), where Q_IJ = sqrt(max_{mu in I, nu in J} (mu nu|mu nu)).  A pair is
+ * kept iff its atoms are closer than 2 r_c (or identical, or r_c <= 0: NAO/orbital-
+ * cutoff screening, Sec. 3.1) and Q_IJ Q_max >= tau.  Each unique quartet is evaluated
+ * once (eight-fold permutational symmetry, Sec. 3.1) by CUDA kernels.
+ *
+ * Basis functions: chi_{I,m}(r) = N_I S_m(r - A) sum_k c_k alpha_k^{(2l+3)/4}
+ * exp(-alpha_k |r - A|^2), with S_m = 1; x, y, z; xy, yz, (3z^2 - r^2)/(2 sqrt 3), xz,
+ * (x^2 - y^2)/2 and N_I such that every function has unit self-overlap.  Function
+ * order: shells in input order, components in the order just listed.
+ *
+ * Conventions for every entry point:
+ *   - Return value: HFX_OK (0) on success, a negative HFX_ERR_* code otherwise; the
+ *     message of the last failure is available from hfx_last_error().  The library
+ *     never aborts the process and has no CPU fallback: without a CUDA device every
+ *     call that needs one fails with HFX_ERR_CUDA.
+ *   - Device pointers are CUDA global-memory addresses on the current device; host
+ *     pointers are ordinary process memory.  The caller owns every buffer it passes;
+ *     the library owns what it allocates inside a context and frees it in hfx_free().
+ *   - Matrices are dense, FP64, row-major with leading dimension ld >= n_bf.
+ *   - Work is ordered on the context's CUDA stream; "async" calls return before the
+ *     GPU work ends.  Calls on one context are not thread-safe.
+ */
+#ifndef HFX_H
+#define HFX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define HFX_OK 0
+#define HFX_ERR_ARG -1            /* invalid argument (null pointer, bad size or index) */
+#define HFX_ERR_UNSUPPORTED_L -2  /* shell angular momentum outside 0..2 */
+#define HFX_ERR_OOM -3            /* device allocation failed */
+#define HFX_ERR_CUDA -4           /* a CUDA call or kernel launch failed */
+#define HFX_ERR_STATE -5          /* call order violated (e.g. build_K before build_pairs) */
+#define HFX_ERR_TIMEOUT -6        /* a bounded device wait gave up */
+
+/* precision modes */
+#define HFX_FP64 0                /* every integral in FP64 */
+#define HFX_MIXED 1               /* small-bound s,p quartets in FP32, see hfx_options */
+
+/* work schedules inside a class launch (paper Sec. 3.2, Algorithms 2 and 3) */
+#define HFX_SCHED_QUARTET 0       /* even split of the screened quartet list (default) */
+#define HFX_SCHED_PAIR 1          /* even split of the bra pair list, screening after */
+
+typedef struct hfx_ctx hfx_ctx;   /* opaque, library-owned */
+
+typedef struct {
+  double omega;        /* range-separation parameter (bohr^-1); 0 gives the Coulomb kernel */
+  double schwarz_tau;  /* Schwarz threshold tau (>= 0) */
+  double rcut_bohr;    /* orbital cutoff radius r_c; <= 0 disables the pair-distance screen */
+  double prim_tau;     /* primitive pairs with |prefactor| below this are dropped (default 1e-22) */
+  int precision;       /* HFX_FP64 (only mode of this version) */
+  int schedule;        /* HFX_SCHED_QUARTET or HFX_SCHED_PAIR */
+  int reserved[6];     /* set to 0 */
+} hfx_options;
+
+typedef struct {
+  int64_t n_pairs_cutoff;      /* shell pairs passing the orbital cutoff */
+  int64_t n_pairs_kept;        /* ... and the pair Schwarz test */
+  int64_t n_quartets;          /* canonical shell quartets kept (Schwarz + cutoff) */
+  int64_t n_quartets_class[21];/* per class, index hi*(hi+1)/2 + lo over pair classes
+                                  ss, ps, pp, ds, dp, dd */
+  int64_t prim_quartets_class[21]; /* primitive quartets evaluated per class (timed builds) */
+  double flops_fp64;           /* FP64 flops of the last timed K build (operation-count model
+                                  of the kernels: add/mul = 1, fma = 2) */
+  double flops_class[21];      /* the same per class */
+  int32_t group_size_class[21];/* lanes per quartet of each class kernel (1 or 32) */
+  double ms_pairs;             /* GPU time of the last hfx_build_pairs */
+  double ms_build;             /* GPU time of the last hfx_build_K (zero K .. E_K ready) */
+  double ms_class[21];         /* GPU time of each class launch in the last K build */
+  double energy;               /* E_K = sum_{mu nu} P_{mu nu} K_{mu nu} of the last K build */
+} hfx_stats;
+
+/* Fills *opt with defaults: omega 0.11, tau 1e-10, no cutoff, prim_tau 1e-22, FP64,
+ * quartet schedule. */
+void hfx_default_options(hfx_options* opt);
+
+/* Creates a context for one system and uploads its basis.
+ *   n_atoms, xyz[3*n_atoms]: atom positions in bohr (host).
+ *   n_shells, shell_atom[n_shells] (0-based atom of each shell), shell_l[n_shells]
+ *   (0..2), shell_nprim[n_shells] (>= 1, <= 8): host arrays.
+ *   alpha[], coef[]: exponents (> 0) and raw contraction weights of all primitives,
+ *   shell after shell (host; the library normalises, see the header comment).
+ *   opt: options (host, may be NULL for defaults).  stream: cudaStream_t to order
+ *   all work of this context on (NULL = default stream).
+ * On success *out receives the context.  Basis upload and normalisation are queued
+ * on the stream.  Errors: HFX_ERR_ARG, HFX_ERR_UNSUPPORTED_L, HFX_ERR_OOM, HFX_ERR_CUDA. */
+int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int n_shells,
+                   const int* shell_atom, const int* shell_l, const int* shell_nprim,
+                   const double* alpha, const double* coef, const hfx_options* opt,
+                   void* stream);
+
+/* Builds the screened shell-pair list (Sec. 3.1: list-IJ = list-KL here, one cell):
+ * orbital-cutoff test, primitive-pair data, Schwarz diagonal Q_IJ by the ERI kernels,
+ * pair Schwarz test, binning by pair class with Q descending, and the per-class
+ * quartet task lists (bra pair -> number of ket pairs passing Q_IJ Q_KL >= tau) with
+ * their 64-bit prefix sums.  The list depends on the basis only, not on P.
+ * Synchronises the stream once (sizes are read back to size the launches). */
+int hfx_build_pairs(hfx_ctx* ctx);
+
+/* Builds K for the density P (both device pointers, n_bf x n_bf, leading dimension
+ * ld; P symmetric).  K is overwritten completely.  Asynchronous on the context stream;
+ * E_K lands in a device scalar (read it with hfx_energy or hfx_get_stats).
+ * Errors: HFX_ERR_STATE (no pair list), HFX_ERR_ARG, HFX_ERR_CUDA. */
+int hfx_build_K(hfx_ctx* ctx, const double* P_dev, double* K_dev, int ld);
+
+/* Same computation with host buffers: copies P (host, n_bf x n_bf row-major) to the
+ * device, builds K, copies K back into K_host and returns after the copy ends.  The
+ * device staging buffers are owned by the context. */
+int hfx_build_K_host(hfx_ctx* ctx, const double* P_host, double* K_host);
+
+/* Device pointer to the FP64 scalar E_K of the last K build (valid until hfx_free). */
+const double* hfx_energy_device(const hfx_ctx* ctx);
+
+/* Synchronises the stream and copies E_K of the last build to *out. */
+int hfx_energy(hfx_ctx* ctx, double* out);
+
+/* Synchronises the stream and fills *out (timings need HFX timing enabled, see
+ * hfx_set_timing). */
+int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out);
+
+/* Enables (1) or disables (0) per-class CUDA-event timing of K builds. */
+int hfx_set_timing(hfx_ctx* ctx, int enable);
+
+/* Number of basis functions of the context, or a negative error code. */
+int hfx_n_basis(const hfx_ctx* ctx);
+
+/* Copies the kept pairs (shell a, shell b with l_a >= l_b, Q) in bin order to host
+ * arrays of length >= max_n; returns the number of kept pairs or an error code. */
+int64_t hfx_get_pairs(hfx_ctx* ctx, int* shell_a, int* shell_b, double* q, int64_t max_n);
+
+/* Per-SM load record of the last K build: for each of n_slots CTA slots, the
+ * globaltimer start and end (ns) of its ERI work, summed over class launches
+ * (busy_ns[n]); returns the number of entries written. */
+int hfx_get_cta_busy(hfx_ctx* ctx, double* busy_ns, int max_n);
+
+/* Message of the last failure on this context ("" if none); ctx may be NULL for
+ * failures of hfx_init_basis. */
+const char* hfx_last_error(const hfx_ctx* ctx);
+
+/* Releases the context and all device memory it owns (synchronises the stream). */
+void hfx_free(hfx_ctx* ctx);
+
+/* Measures the FP64 and FP32 fused-multiply-add throughput of the current device with
+ * a register-resident FMA chain (TFLOP/s, FMA = 2 flops).  Used as the roofline
+ * denominators for the FP64/FP32 ALU-bound kernels. */
+int hfx_measure_fma_peak(double* fp64_tflops, double* fp32_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HFX_H */

@@ -1,0 +1,498 @@
+#!/usr/bin/env python3
+"""Generate the per-class recurrence tables of the table-driven ERI engine.
+
+For every shell-quartet class (la lb | lc ld) with la >= lb, lc >= ld and bra pair
+class >= ket pair class (21 classes for s, p, d shells) this emits:
+
+* the vertical recurrence (Obara-Saika, in the Head-Gordon-Pople arrangement) as
+  levels of independent ops over shared-memory slots:
+      bra  [e+1_i 0|00]^(m) = PA_i [e]^(m) + WP_i [e]^(m+1)
+                              + e_i/(2p) ([e-1_i]^(m) - rho/p [e-1_i]^(m+1))
+      ket  [e0|f+1_i 0]^(m) = QC_i [e|f]^(m) + WQ_i [e|f]^(m+1)
+                              + f_i/(2q) ([e|f-1_i]^(m) - rho/q [e|f-1_i]^(m+1))
+                              + e_i/(2(p+q)) [e-1_i|f]^(m+1)
+  pruned to what the targets [e0|f0]^(0), e in [la, la+lb], f in [lc, lc+ld], need;
+* the contraction list (VRR slot -> accumulator);
+* the horizontal recurrence (Head-Gordon-Pople) on bra then ket:
+      (a, b+1_i| = (a+1_i, b| + AB_i (a, b|,   |c, d+1_i) = |c+1_i, d) + CD_i |c, d);
+* the Cartesian -> spherical step for d shells, real solid harmonics in the order
+  xy, yz, 3z^2-r^2, xz, x^2-y^2 with the relative factors 1, 1, 1/(2 sqrt 3), 1, 1/2
+  (all five then share one radial normalisation);
+* FP64 operation counts per primitive quartet and per contracted quartet.
+
+The output is a C header consumed by the CUDA library (``eri_tables.inc``).  Run:
+    python gen_eri_tables.py > eri_tables.inc
+"""
+from __future__ import annotations
+
+import json
+import math
+import sys
+
+PAIR_CLASSES = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+
+
+def monos(l):
+    """Cartesian monomials of degree l in the order xx, xy, xz, yy, yz, zz (for l = 2)."""
+    return [(i, j, l - i - j) for i in range(l, -1, -1) for j in range(l - i, -1, -1)]
+
+
+def ncart(l):
+    return (l + 1) * (l + 2) // 2
+
+
+def sub1(v, i):
+    w = list(v)
+    w[i] -= 1
+    return tuple(w)
+
+
+def add1(v, i):
+    w = list(v)
+    w[i] += 1
+    return tuple(w)
+
+
+def deg(v):
+    return v[0] + v[1] + v[2]
+
+
+def vrr_dir(v):
+    """Axis with the smallest positive power: avoids the (e-1_i) term where possible."""
+    best = None
+    for i in range(3):
+        if v[i] > 0 and (best is None or v[i] < v[best]):
+            best = i
+    return best
+
+
+def hrr_dir(v):
+    for i in range(3):
+        if v[i] > 0:
+            return i
+    return None
+
+
+# coefficient table for the Cartesian -> spherical step (indices into SPH_COEF)
+S3 = 1.0 / (2.0 * math.sqrt(3.0))
+SPH_COEF = [0.0, 1.0, -S3, 2.0 * S3, 0.5, -0.5]
+# rows: spherical component; entries: (cartesian index in monos(2), coefficient index)
+SPH_D = [
+    [(1, 1)],                       # xy
+    [(4, 1)],                       # yz
+    [(5, 3), (0, 2), (3, 2)],       # (2zz - xx - yy) / (2 sqrt 3)
+    [(2, 1)],                       # xz
+    [(0, 4), (3, 5)],               # (xx - yy) / 2
+]
+
+
+def nsph(l):
+    return 2 * l + 1
+
+
+class ClassTables:
+    def __init__(self, la, lb, lc, ld):
+        self.la, self.lb, self.lc, self.ld = la, lb, lc, ld
+        self.E, self.F = la + lb, lc + ld
+        self.Lt = self.E + self.F
+        self.build()
+
+    # ------------------------------------------------------------------ VRR
+    def build(self):
+        la, lb, lc, ld, E, F, Lt = self.la, self.lb, self.lc, self.ld, self.E, self.F, self.Lt
+        targets = [(e, f, 0) for de in range(la, E + 1) for e in monos(de)
+                   for df in range(lc, F + 1) for f in monos(df)]
+        need = set()
+        stack = list(targets)
+        deps = {}
+        while stack:
+            k = stack.pop()
+            if k in need:
+                continue
+            need.add(k)
+            e, f, m = k
+            d = []
+            if deg(f) > 0:
+                i = vrr_dir(f)
+                f1 = sub1(f, i)
+                d += [(e, f1, m), (e, f1, m + 1)]
+                if f1[i] > 0:
+                    f2 = sub1(f1, i)
+                    d += [(e, f2, m), (e, f2, m + 1)]
+                if e[i] > 0:
+                    d += [(sub1(e, i), f1, m + 1)]
+            elif deg(e) > 0:
+                i = vrr_dir(e)
+                e1 = sub1(e, i)
+                d += [(e1, f, m), (e1, f, m + 1)]
+                if e1[i] > 0:
+                    e2 = sub1(e1, i)
+                    d += [(e2, f, m), (e2, f, m + 1)]
+            deps[k] = d
+            stack.extend(d)
+        z = (0, 0, 0)
+        # base slots: [00|00]^(m) for m = 0..Lt (all of them, filled by the Boys step)
+        slot = {}
+        for m in range(Lt + 1):
+            slot[(z, z, m)] = m
+        nslot = Lt + 1
+        bra_levels, ket_levels = [], []
+        for de in range(1, E + 1):
+            lvl = sorted([k for k in need if deg(k[1]) == 0 and deg(k[0]) == de],
+                         key=lambda k: (monos(de).index(k[0]), k[2]))
+            for k in lvl:
+                slot[k] = nslot
+                nslot += 1
+            bra_levels.append(lvl)
+        for df in range(1, F + 1):
+            lvl = sorted([k for k in need if deg(k[1]) == df],
+                         key=lambda k: (deg(k[0]), k[0], k[1], k[2]))
+            for k in lvl:
+                slot[k] = nslot
+                nslot += 1
+            ket_levels.append(lvl)
+        self.n_vrr_slots = nslot
+        self.slot = slot
+        # ops
+        self.bra_ops = []
+        for lvl in bra_levels:
+            ops = []
+            for k in lvl:
+                e, f, m = k
+                i = vrr_dir(e)
+                e1 = sub1(e, i)
+                n = e1[i]
+                s1, s2 = slot[(e1, f, m)], slot[(e1, f, m + 1)]
+                s3 = s4 = 0
+                if n > 0:
+                    e2 = sub1(e1, i)
+                    s3, s4 = slot[(e2, f, m)], slot[(e2, f, m + 1)]
+                ops.append(dict(dst=slot[k], s=[s1, s2, s3, s4, 0], dir=i, nA=n, nB=0))
+            ops.sort(key=lambda o: (o["nA"] > 0, o["dst"]))
+            self.bra_ops.append(ops)
+        self.ket_ops = []
+        for lvl in ket_levels:
+            ops = []
+            for k in lvl:
+                e, f, m = k
+                i = vrr_dir(f)
+                f1 = sub1(f, i)
+                n = f1[i]
+                s1, s2 = slot[(e, f1, m)], slot[(e, f1, m + 1)]
+                s3 = s4 = s5 = 0
+                if n > 0:
+                    f2 = sub1(f1, i)
+                    s3, s4 = slot[(e, f2, m)], slot[(e, f2, m + 1)]
+                nB = e[i]
+                if nB > 0:
+                    s5 = slot[(sub1(e, i), f1, m + 1)]
+                ops.append(dict(dst=slot[k], s=[s1, s2, s3, s4, s5], dir=i, nA=n, nB=nB))
+            ops.sort(key=lambda o: (o["nA"] > 0, o["nB"] > 0, o["dst"]))
+            self.ket_ops.append(ops)
+        # accumulators: e over degrees la..E (ordered), f over lc..F
+        self.e_list = [e for de in range(la, E + 1) for e in monos(de)]
+        self.f_list = [f for df in range(lc, F + 1) for f in monos(df)]
+        self.n_acc = len(self.e_list) * len(self.f_list)
+        self.acc_src = []
+        for ie, e in enumerate(self.e_list):
+            for jf, f in enumerate(self.f_list):
+                self.acc_src.append(slot[(e, f, 0)])
+        self.build_hrr()
+
+    # ------------------------------------------------------------------ HRR + sph
+    def build_hrr(self):
+        """Post-contraction stages, each reading only the previous stage's block:
+        bra HRR levels -> sph(a) -> sph(b) -> ket HRR levels -> sph(c) -> sph(d).
+        A stage is a list of (dst_index, [(src_index, kind_or_coef)], dir); indices
+        are positions in the previous / current stage's block."""
+        la, lb, lc, ld, E, F = self.la, self.lb, self.lc, self.ld, self.E, self.F
+        z = (0, 0, 0)
+        # stage 0: the accumulator block, keys (a, b, f) with b = 0
+        cur_keys = [(e, z, f) for e in self.e_list for f in self.f_list]
+        self.stages = []       # each: dict(type, ops=[(dst, srcs, dir)]) with srcs indices into prev block
+        self.stage_sizes = [len(cur_keys)]
+
+        def add_stage(kind, new_keys, make_srcs):
+            nonlocal cur_keys
+            idx = {k: i for i, k in enumerate(cur_keys)}
+            ops = []
+            for j, k in enumerate(new_keys):
+                srcs, d = make_srcs(k)
+                ops.append((j, [(idx[sk], c) for sk, c in srcs], d))
+            self.stages.append(dict(type=kind, ops=ops))
+            self.stage_sizes.append(len(new_keys))
+            cur_keys = new_keys
+
+        # bra HRR: (a, b + 1_i | f) = (a + 1_i, b | f) + AB_i (a, b | f)
+        for db in range(1, lb + 1):
+            new = [(a, b, f) for da in range(la, E - db + 1) for a in monos(da)
+                   for b in monos(db) for f in self.f_list]
+
+            def mk(k):
+                a, b, f = k
+                i = hrr_dir(b)
+                b1 = sub1(b, i)
+                return [((add1(a, i), b1, f), 1), ((a, b1, f), 2)], i
+            add_stage("hrr_bra", new, mk)
+        # keys are now (a, b, f) with deg a = la, deg b = lb; move to spherical a, b
+        # representation: key (ka, kb, f) where ka/kb are Cartesian tuples or ("s", m)
+        ls = [la, lb]
+        for t in range(2):
+            if ls[t] != 2:
+                continue
+            old = cur_keys
+            comps = []
+            for k in old:
+                kk = list(k)
+                kk[t] = None
+                comps.append(tuple(kk))
+            seen = []
+            for c in comps:
+                if c not in seen:
+                    seen.append(c)
+            new = []
+            for c in seen:
+                for m in range(5):
+                    kk = list(c)
+                    kk[t] = ("s", m)
+                    new.append(tuple(kk))
+            # order: row-major over (a, b, f)
+            new = self._order3(new)
+
+            def mk(k, t=t):
+                m = k[t][1]
+                srcs = []
+                for (cc, ci) in SPH_D[m]:
+                    kk = list(k)
+                    kk[t] = monos(2)[cc]
+                    srcs.append((tuple(kk), ci))
+                return srcs, 0
+            add_stage("sph", new, mk)
+        # ket HRR on f: |c, d + 1_i) = |c + 1_i, d) + CD_i |c, d); keys become (a, b, c, d)
+        cur_keys = [(a, b, f, z) for (a, b, f) in cur_keys]
+        AB_keys = []
+        for (a, b, f, d) in cur_keys:
+            if (a, b) not in AB_keys:
+                AB_keys.append((a, b))
+        for dd in range(1, ld + 1):
+            new = [(a, b, c, d) for (a, b) in AB_keys for dc in range(lc, F - dd + 1)
+                   for c in monos(dc) for d in monos(dd)]
+
+            def mk(k):
+                a, b, c, d = k
+                i = hrr_dir(d)
+                d1 = sub1(d, i)
+                return [((a, b, add1(c, i), d1), 1), ((a, b, c, d1), 2)], i
+            add_stage("hrr_ket", new, mk)
+        ls2 = [lc, ld]
+        for t in (2, 3):
+            if ls2[t - 2] != 2:
+                continue
+            old = cur_keys
+            seen = []
+            for k in old:
+                kk = list(k)
+                kk[t] = None
+                kk = tuple(kk)
+                if kk not in seen:
+                    seen.append(kk)
+            new = []
+            for c in seen:
+                for m in range(5):
+                    kk = list(c)
+                    kk[t] = ("s", m)
+                    new.append(tuple(kk))
+            new = sorted(new, key=lambda k: tuple(self._comp_order(k[u]) for u in range(4)))
+
+            def mk(k, t=t):
+                m = k[t][1]
+                srcs = []
+                for (cc, ci) in SPH_D[m]:
+                    kk = list(k)
+                    kk[t] = monos(2)[cc]
+                    srcs.append((tuple(kk), ci))
+                return srcs, 0
+            add_stage("sph", new, mk)
+        if len(cur_keys[0]) == 3:
+            cur_keys = [(a, b, f, z) for (a, b, f) in cur_keys]
+        # final block must be row-major (a, b, c, d) over the final components
+        self.final_dims = [nsph(la) if la == 2 else ncart(la), nsph(lb) if lb == 2 else ncart(lb),
+                           nsph(lc) if lc == 2 else ncart(lc), nsph(ld) if ld == 2 else ncart(ld)]
+        n = 1
+        for d in self.final_dims:
+            n *= d
+        assert len(cur_keys) == n, (self.name(), len(cur_keys), n)
+        self._check_row_major(cur_keys)
+
+    @staticmethod
+    def _comp_order(c, l_hint=None):
+        if isinstance(c, tuple) and len(c) == 2 and c[0] == "s":
+            return (1, c[1])
+        return (0, monos(deg(c)).index(c))
+
+    def _order3(self, keys):
+        # keep the f order of self.f_list
+        fpos = {f: i for i, f in enumerate(self.f_list)}
+        return sorted(keys, key=lambda k: (self._comp_order(k[0]), self._comp_order(k[1]), fpos[k[2]]))
+
+    def _check_row_major(self, keys):
+        orders = [sorted({self._comp_order(k[t]) for k in keys}) for t in range(4)]
+        exp = []
+        for a in orders[0]:
+            for b in orders[1]:
+                for c in orders[2]:
+                    for d in orders[3]:
+                        exp.append((a, b, c, d))
+        got = [tuple(self._comp_order(k[t]) for t in range(4)) for k in keys]
+        assert got == exp, self.name()
+
+    def name(self):
+        L = "spd"
+        return f"{L[self.la]}{L[self.lb]}{L[self.lc]}{L[self.ld]}"
+
+    # ------------------------------------------------------------------ counts
+    def flops(self):
+        """FP64 flops (fma = 2) of the recurrence parts."""
+        vrr = 0
+        for lvl in self.bra_ops:
+            for o in lvl:
+                vrr += 3 + (4 if o["nA"] else 0)            # mul+fma [+ fma + fma]
+        for lvl in self.ket_ops:
+            for o in lvl:
+                vrr += 3 + (4 if o["nA"] else 0) + (2 if o["nB"] else 0)
+        acc = self.n_acc
+        hrr = sph = 0
+        for st in self.stages:
+            for _, srcs, _ in st["ops"]:
+                if st["type"] == "sph":
+                    sph += 2 * len(srcs) - 1
+                else:
+                    hrr += 2
+        nout = 1
+        for d in self.final_dims:
+            nout *= d
+        na, nb, nc, nd = self.final_dims
+        digest = 2 * nout * 4 + (na * nc + na * nd + nb * nc + nb * nd)
+        return dict(vrr=vrr, acc=acc, hrr=hrr, sph=sph, digest=digest, nout=nout)
+
+    # ------------------------------------------------------------------ layout
+    def layout(self):
+        """Group scratch (doubles): acc block at 0 and the VRR slots after it while the
+        primitive loop runs; afterwards the stages alternate between the bottom (offset
+        0) and the top (ending at the scratch size) of the same scratch."""
+        sizes = self.stage_sizes
+        T = self.n_acc + self.n_vrr_slots
+        for k in range(1, len(sizes)):
+            T = max(T, sizes[k - 1] + sizes[k])
+        bases = [0]
+        for k in range(1, len(sizes)):
+            bases.append(T - sizes[k] if k % 2 == 1 else 0)
+        return T, bases
+
+
+def pack_vrr(o):
+    """uint4 op: dst|s1, s2|s3, s4|s5 (16 bits each), dir | nA << 2 | nB << 5."""
+    s = o["s"]
+    return [(o["dst"] & 0xFFFF) | ((s[0] & 0xFFFF) << 16),
+            (s[1] & 0xFFFF) | ((s[2] & 0xFFFF) << 16),
+            (s[3] & 0xFFFF) | ((s[4] & 0xFFFF) << 16),
+            o["dir"] | (o["nA"] << 2) | (o["nB"] << 5)]
+
+
+def all_classes():
+    out = []
+    for hi in range(6):
+        for lo in range(hi + 1):
+            la, lb = PAIR_CLASSES[hi]
+            lc, ld = PAIR_CLASSES[lo]
+            out.append(ClassTables(la, lb, lc, ld))
+    return out
+
+
+STAGE_TYPE = {"hrr_bra": 0, "hrr_ket": 1, "sph": 2}
+
+
+def emit(classes, f=sys.stdout):
+    w = f.write
+    w("// Generated by gen_eri_tables.py -- do not edit by hand.\n")
+    w("// Per-class Obara-Saika / Head-Gordon-Pople recurrence tables for the FP64 engine.\n")
+    w("#pragma once\n\n")
+    vrr_words, post_words, acc_words = [], [], []
+    rows = []
+    for c in classes:
+        T, bases = c.layout()
+        work_base = c.n_acc
+        lv_off, lv_n = [], []
+        for lvl in c.bra_ops + c.ket_ops:
+            lv_off.append(len(vrr_words) // 4)
+            lv_n.append(len(lvl))
+            for o in lvl:
+                vrr_words.extend(pack_vrr(o))
+        acc_off = len(acc_words)
+        acc_words.extend(c.acc_src)
+        p_type, p_off, p_n = [], [], []
+        for k, st in enumerate(c.stages):
+            src_base = bases[k]
+            dst_base = bases[k + 1]
+            p_type.append(STAGE_TYPE[st["type"]])
+            p_off.append(len(post_words) // 4)
+            p_n.append(len(st["ops"]))
+            for (dst, srcs, d) in st["ops"]:
+                sl = [src_base + s for s, _ in srcs] + [0] * (3 - len(srcs))
+                cs = [cc for _, cc in srcs] + [0] * (3 - len(srcs))
+                if st["type"] != "sph":
+                    cs = [0, 0, 0]
+                post_words.extend([((dst_base + dst) & 0xFFFF) | ((sl[0] & 0xFFFF) << 16),
+                                   (sl[1] & 0xFFFF) | ((sl[2] & 0xFFFF) << 16),
+                                   cs[0] | (cs[1] << 4) | (cs[2] << 8) | (d << 12),
+                                   0])
+        out_base = bases[len(c.stages)]
+        fl = c.flops()
+        rows.append(dict(c=c, T=T, work_base=work_base, lv_off=lv_off, lv_n=lv_n, acc_off=acc_off,
+                         p_type=p_type, p_off=p_off, p_n=p_n, out_base=out_base, fl=fl))
+
+    def arr(name, words, per_line=8):
+        w(f"HFX_TABLE_QUAL uint32_t {name}[{max(len(words), 4)}] = {{\n")
+        ws = words if words else [0, 0, 0, 0]
+        for i in range(0, len(ws), per_line):
+            w("  " + ", ".join(f"{x}u" for x in ws[i:i + per_line]) + ",\n")
+        w("};\n\n")
+
+    w(f"#define HFX_N_CLASSES {len(classes)}\n\n")
+    w("static const double kSphCoefHost[6] = {" + ", ".join(repr(x) for x in SPH_COEF) + "};\n\n")
+    arr("kVrrOps", vrr_words)
+    arr("kPostOps", post_words)
+    arr("kAccSrc", acc_words)
+
+    def lst(v, n):
+        v = list(v) + [0] * (n - len(v))
+        assert len(v) == n
+        return "{" + ", ".join(str(x) for x in v) + "}"
+    w("static const EriClassInfo kClassInfo[HFX_N_CLASSES] = {\n")
+    for r in rows:
+        c, fl = r["c"], r["fl"]
+        w(f"  // ({c.name()}) vrr {fl['vrr']} flop/prim + acc {fl['acc']}; per quartet hrr {fl['hrr']}, "
+          f"sph {fl['sph']}, digest {fl['digest']}; scratch {r['T']} doubles\n")
+        w("  {" + ", ".join([
+            str(c.la), str(c.lb), str(c.lc), str(c.ld), str(c.E), str(c.F), str(c.Lt),
+            str(c.n_acc), str(r["work_base"]), str(r["T"]),
+            str(len(c.bra_ops)), str(len(c.ket_ops)),
+            lst(r["lv_off"], 8), lst(r["lv_n"], 8), str(r["acc_off"]),
+            str(len(c.stages)), lst(r["p_type"], 8), lst(r["p_off"], 8), lst(r["p_n"], 8),
+            str(r["out_base"]), lst(c.final_dims, 4),
+            str(fl["vrr"] + fl["acc"]), str(fl["hrr"] + fl["sph"] + fl["digest"]),
+        ]) + "},\n")
+    w("};\n")
+
+
+if __name__ == "__main__":
+    cl = all_classes()
+    if len(sys.argv) > 1 and sys.argv[1] == "--summary":
+        for c in cl:
+            fl = c.flops()
+            T, bases = c.layout()
+            print(f"{c.name()}: vrr_slots {c.n_vrr_slots} acc {c.n_acc} scratch {T} "
+                  f"stages {[st['type'] for st in c.stages]} sizes {c.stage_sizes} "
+                  f"levels {[len(l) for l in c.bra_ops + c.ket_ops]} flops {json.dumps(fl)}")
+    else:
+        emit(cl)

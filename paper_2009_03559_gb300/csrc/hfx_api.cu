@@ -1,0 +1,571 @@
+// C ABI of the HFX library: context, basis upload, pair-list build, K build.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hfx.h"
+#include "hfx_eri.h"
+#include "hfx_internal.cuh"
+#include "hfx_setup.h"
+
+using namespace hfx;
+
+struct hfx_ctx {
+  cudaStream_t stream = nullptr;
+  hfx_options opt{};
+  std::string err;
+  int n_atoms = 0, n_shells = 0, n_bf = 0, n_prim = 0, n_sm = 0;
+  std::vector<int> h_l;
+  // basis (device)
+  double *d_xyz = nullptr, *d_alpha = nullptr, *d_coef = nullptr, *d_w = nullptr, *d_boys = nullptr;
+  int *d_atom = nullptr, *d_l = nullptr, *d_nprim = nullptr, *d_prim_off = nullptr, *d_bf_off = nullptr;
+  // pairs (device)
+  int n_cand = 0, n_kept = 0;
+  int *d_sa = nullptr, *d_sb = nullptr, *d_pcls = nullptr, *d_pp_off = nullptr, *d_pp_n = nullptr;
+  double *d_AB = nullptr, *d_Q = nullptr, *d_Qs = nullptr;
+  PrimPair* d_pp = nullptr;
+  int* d_sorted = nullptr;
+  RowTable rt{};
+  int n_rows = 0;
+  long long* d_qoff = nullptr;
+  long long cls_q[21] = {}, cls_qbegin[21] = {};
+  bool pairs_ready = false;
+  // per build
+  double *d_energy = nullptr, *d_part = nullptr;
+  int n_part = 0;
+  double *d_Pst = nullptr, *d_Kst = nullptr;
+  unsigned long long* d_busy = nullptr;      // per SM
+  unsigned long long* d_counters = nullptr;  // 3 per class
+  bool timing = false;
+  cudaEvent_t ev[2 * 21 + 4] = {};
+  bool ev_ok = false;
+  bool class_launched[21] = {};
+  hfx_stats stats{};
+  float ms_pairs = 0.f;
+  std::vector<void*> allocs;       // owned for the context lifetime
+  std::vector<void*> pair_allocs;  // owned until the next build_pairs
+
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+  int cuda_fail(const char* what, cudaError_t e) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? HFX_ERR_OOM : HFX_ERR_CUDA;
+  }
+  template <class T>
+  int alloc(T** p, size_t n, bool pair_scope = false) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail("cudaMalloc", e);
+    (pair_scope ? pair_allocs : allocs).push_back(*p);
+    return HFX_OK;
+  }
+  void free_pairs() {
+    for (void* p : pair_allocs) cudaFree(p);
+    pair_allocs.clear();
+    pairs_ready = false;
+  }
+};
+
+static thread_local std::string g_init_err;
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return ctx->cuda_fail(#call, e_); \
+  } while (0)
+#define RK(call)                 \
+  do {                           \
+    int r_ = (call);             \
+    if (r_ != HFX_OK) return r_; \
+  } while (0)
+
+extern "C" void hfx_default_options(hfx_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->omega = 0.11;
+  opt->schwarz_tau = 1e-10;
+  opt->rcut_bohr = 0.0;
+  opt->prim_tau = 1e-22;
+  opt->precision = HFX_FP64;
+  opt->schedule = HFX_SCHED_QUARTET;
+}
+
+extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int n_shells,
+                              const int* shell_atom, const int* shell_l, const int* shell_nprim,
+                              const double* alpha, const double* coef, const hfx_options* opt, void* stream) {
+  g_init_err.clear();
+  if (!out) {
+    g_init_err = "out is NULL";
+    return HFX_ERR_ARG;
+  }
+  *out = nullptr;
+  if (n_atoms <= 0 || n_shells <= 0 || !xyz || !shell_atom || !shell_l || !shell_nprim || !alpha || !coef) {
+    g_init_err = "empty basis or NULL array";
+    return HFX_ERR_ARG;
+  }
+  hfx_options o;
+  hfx_default_options(&o);
+  if (opt) o = *opt;
+  if (!(o.omega >= 0.0) || !(o.schwarz_tau >= 0.0) || !(o.prim_tau >= 0.0) || o.precision != HFX_FP64 ||
+      (o.schedule != HFX_SCHED_QUARTET && o.schedule != HFX_SCHED_PAIR)) {
+    g_init_err = "invalid options";
+    return HFX_ERR_ARG;
+  }
+  std::vector<int> prim_off(n_shells), bf_off(n_shells);
+  int np = 0, nb = 0;
+  for (int s = 0; s < n_shells; ++s) {
+    if (shell_l[s] < 0 || shell_l[s] > 2) {
+      g_init_err = "shell " + std::to_string(s) + ": angular momentum " + std::to_string(shell_l[s]) +
+                   " outside 0..2";
+      return HFX_ERR_UNSUPPORTED_L;
+    }
+    if (shell_nprim[s] < 1 || shell_nprim[s] > 8 || shell_atom[s] < 0 || shell_atom[s] >= n_atoms) {
+      g_init_err = "shell " + std::to_string(s) + ": bad primitive count or atom index";
+      return HFX_ERR_ARG;
+    }
+    prim_off[s] = np;
+    bf_off[s] = nb;
+    np += shell_nprim[s];
+    nb += 2 * shell_l[s] + 1;
+  }
+  for (int k = 0; k < np; ++k)
+    if (!(alpha[k] > 0.0) || !std::isfinite(coef[k])) {
+      g_init_err = "primitive " + std::to_string(k) + ": exponent must be > 0 and weight finite";
+      return HFX_ERR_ARG;
+    }
+  for (int a = 0; a < 3 * n_atoms; ++a)
+    if (!std::isfinite(xyz[a])) {
+      g_init_err = "non-finite coordinate";
+      return HFX_ERR_ARG;
+    }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    g_init_err = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    return HFX_ERR_CUDA;
+  }
+  hfx_ctx* ctx = new hfx_ctx();
+  ctx->stream = (cudaStream_t)stream;
+  ctx->opt = o;
+  ctx->n_atoms = n_atoms;
+  ctx->n_shells = n_shells;
+  ctx->n_bf = nb;
+  ctx->n_prim = np;
+  ctx->h_l.assign(shell_l, shell_l + n_shells);
+  cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  auto bail = [&](int code) {
+    g_init_err = ctx->err;
+    hfx_free(ctx);
+    return code;
+  };
+  int r;
+  if ((r = ctx->alloc(&ctx->d_xyz, 3 * (size_t)n_atoms)) || (r = ctx->alloc(&ctx->d_alpha, np)) ||
+      (r = ctx->alloc(&ctx->d_coef, np)) || (r = ctx->alloc(&ctx->d_w, np)) ||
+      (r = ctx->alloc(&ctx->d_boys, (size_t)kBoysRows * kBoysCols)) || (r = ctx->alloc(&ctx->d_atom, n_shells)) ||
+      (r = ctx->alloc(&ctx->d_l, n_shells)) || (r = ctx->alloc(&ctx->d_nprim, n_shells)) ||
+      (r = ctx->alloc(&ctx->d_prim_off, n_shells)) || (r = ctx->alloc(&ctx->d_bf_off, n_shells)) ||
+      (r = ctx->alloc(&ctx->d_energy, 1)) || (r = ctx->alloc(&ctx->d_busy, 1024)) ||
+      (r = ctx->alloc(&ctx->d_counters, 3 * 21)))
+    return bail(r);
+  ctx->n_part = 2 * ctx->n_sm;
+  if ((r = ctx->alloc(&ctx->d_part, 2 * (size_t)ctx->n_part))) return bail(r);
+  cudaStream_t s = ctx->stream;
+#define CKI(call)                                                   \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return bail(ctx->cuda_fail(#call, e_)); \
+  } while (0)
+  CKI(cudaMemcpyAsync(ctx->d_xyz, xyz, sizeof(double) * 3 * n_atoms, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(ctx->d_alpha, alpha, sizeof(double) * np, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(ctx->d_coef, coef, sizeof(double) * np, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(ctx->d_atom, shell_atom, sizeof(int) * n_shells, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(ctx->d_l, shell_l, sizeof(int) * n_shells, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(ctx->d_nprim, shell_nprim, sizeof(int) * n_shells, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(ctx->d_prim_off, prim_off.data(), sizeof(int) * n_shells, cudaMemcpyHostToDevice, s));
+  CKI(cudaMemcpyAsync(ctx->d_bf_off, bf_off.data(), sizeof(int) * n_shells, cudaMemcpyHostToDevice, s));
+  CKI(launch_normalize(n_shells, ctx->d_l, ctx->d_nprim, ctx->d_prim_off, ctx->d_alpha, ctx->d_coef, ctx->d_w, s));
+  CKI(launch_boys_table(ctx->d_boys, s));
+  CKI(eri_prepare());
+  CKI(cudaStreamSynchronize(s));  // host arrays may be released by the caller after return
+  for (auto& ev : ctx->ev) {
+    if (cudaEventCreate(&ev) != cudaSuccess) return bail(ctx->fail(HFX_ERR_CUDA, "cudaEventCreate"));
+  }
+  ctx->ev_ok = true;
+#undef CKI
+  *out = ctx;
+  return HFX_OK;
+}
+
+// FP64 flops (add/mul 1, fma 2) of one primitive-quartet set-up as written in
+// prim_setup / boys_eval (table branch; the asymptotic branch is not cheaper).
+static double boys_flops(int mmax) { return mmax <= 1 ? 7.0 + 12.0 * (mmax + 1) : 32.0 + 3.0 * mmax; }
+static double setup_flops(int E, int F, int Lt, bool erfc) {
+  double f = 1 + 8 + 3 + 9 + 12 + 2;                   // s, 1/s, rho/p, rho/q, rho, PQ, r2, T, rsqrt, pref
+  if (erfc)
+    f += 11 + 13 + 2 * boys_flops(Lt) + 4.0 * (Lt + 1);  // kappa, kappa^{1/2}, two Boys, G_m
+  else
+    f += boys_flops(Lt) + (Lt + 1);
+  if (E > 0) f += 5;
+  if (F > 0) f += 9;
+  return f;
+}
+// a primitive quartet dropped at kappa T >= table end costs the set-up up to that test
+static double skip_flops() { return 1 + 8 + 3 + 9 + 12 + 2 + 11; }
+
+static EriLaunch base_launch(hfx_ctx* ctx) {
+  EriLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.pa.sa = ctx->d_sa;
+  L.pa.sb = ctx->d_sb;
+  L.pa.prim_off = ctx->d_pp_off;
+  L.pa.prim_n = ctx->d_pp_n;
+  L.pa.AB = ctx->d_AB;
+  L.pa.prim = ctx->d_pp;
+  L.sh.bf_off = ctx->d_bf_off;
+  L.sh.atom = ctx->d_atom;
+  L.boys = ctx->d_boys;
+  L.omega2 = ctx->opt.omega * ctx->opt.omega;
+  L.schedule = ctx->opt.schedule;
+  return L;
+}
+
+static int grid_for(hfx_ctx* ctx, int cls, int mode, long long work_items) {
+  const int gs = eri_group_size(cls);
+  const int groups_per_block = eri_block_size() / gs;
+  long long need = (work_items + groups_per_block - 1) / groups_per_block;
+  long long cap = (long long)eri_blocks_per_sm(cls, mode) * ctx->n_sm;
+  long long g = std::min(need, cap);
+  return (int)std::max(1LL, g);
+}
+
+extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
+  if (!ctx) return HFX_ERR_ARG;
+  ctx->free_pairs();
+  cudaStream_t s = ctx->stream;
+  CK(cudaEventRecord(ctx->ev[44], s));
+  const long long n = ctx->n_shells;
+  const long long n_tri = n * (n + 1) / 2;
+  // 1. candidate pairs passing the orbital cutoff
+  int* d_flag;
+  long long* d_cand_t;
+  int* d_num;
+  RK(ctx->alloc(&d_flag, n_tri, true));
+  RK(ctx->alloc(&d_cand_t, n_tri, true));
+  RK(ctx->alloc(&d_num, 8, true));
+  CK(launch_pair_flags(n_tri, ctx->d_atom, ctx->d_xyz, ctx->opt.rcut_bohr, d_flag, s));
+  size_t tb = 0;
+  CK(select_flagged(nullptr, tb, n_tri, d_flag, d_cand_t, d_num, s));
+  void* tmp;
+  size_t tmp_bytes = std::max<size_t>(tb, 1 << 20);
+  // one temp buffer big enough for every CUB call below (sized conservatively)
+  {
+    size_t t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0;
+    int nn = (int)std::min<long long>(n_tri, 0x7fffffff);
+    CK(scan_int(nullptr, t2, (int*)nullptr, (int*)nullptr, nn, s));
+    CK(sort_int_keys(nullptr, t3, nullptr, nullptr, nullptr, nullptr, nn, 3, s));
+    CK(sort_double_desc(nullptr, t4, nullptr, nullptr, nullptr, nullptr, nn, s));
+    CK(reduce_max(nullptr, t5, nullptr, nullptr, nn, s));
+    CK(scan_ll_inclusive(nullptr, t6, nullptr, nullptr, 6 * nn, s));
+    tmp_bytes = std::max({tmp_bytes, t2, t3, t4, t5, t6});
+  }
+  RK(ctx->alloc((char**)&tmp, tmp_bytes, true));
+  tb = tmp_bytes;
+  CK(select_flagged(tmp, tb, n_tri, d_flag, d_cand_t, d_num, s));
+  int n_cand = 0;
+  CK(cudaMemcpyAsync(&n_cand, d_num, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  ctx->n_cand = n_cand;
+  if (n_cand == 0) return ctx->fail(HFX_ERR_ARG, "no shell pair passes the orbital cutoff");
+  // 2. orientation, class, AB, primitive pairs
+  int* d_cap;
+  RK(ctx->alloc(&ctx->d_sa, n_cand, true));
+  RK(ctx->alloc(&ctx->d_sb, n_cand, true));
+  RK(ctx->alloc(&ctx->d_pcls, n_cand, true));
+  RK(ctx->alloc(&ctx->d_AB, 3 * (size_t)n_cand, true));
+  RK(ctx->alloc(&d_cap, n_cand, true));
+  RK(ctx->alloc(&ctx->d_pp_off, n_cand, true));
+  RK(ctx->alloc(&ctx->d_pp_n, n_cand, true));
+  RK(ctx->alloc(&ctx->d_Q, n_cand, true));
+  CK(launch_pair_setup(n_cand, d_cand_t, ctx->d_l, ctx->d_nprim, ctx->d_atom, ctx->d_xyz, ctx->d_sa, ctx->d_sb,
+                       ctx->d_pcls, ctx->d_AB, d_cap, s));
+  tb = tmp_bytes;
+  CK(scan_int(tmp, tb, d_cap, ctx->d_pp_off, n_cand, s));
+  int last[2];
+  CK(cudaMemcpyAsync(&last[0], ctx->d_pp_off + n_cand - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&last[1], d_cap + n_cand - 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const long long n_pp = (long long)last[0] + last[1];
+  RK(ctx->alloc(&ctx->d_pp, n_pp, true));
+  CK(launch_prim_fill(n_cand, ctx->d_sa, ctx->d_sb, ctx->d_nprim, ctx->d_prim_off, ctx->d_atom, ctx->d_xyz,
+                      ctx->d_alpha, ctx->d_w, ctx->d_pp_off, ctx->opt.prim_tau, ctx->d_pp, ctx->d_pp_n, s));
+  // 3. group candidates by pair class, Schwarz diagonal per class
+  int *d_iota, *d_ckey, *d_cidx, *d_cnt;
+  RK(ctx->alloc(&d_iota, n_cand, true));
+  RK(ctx->alloc(&d_ckey, n_cand, true));
+  RK(ctx->alloc(&d_cidx, n_cand, true));
+  RK(ctx->alloc(&d_cnt, 16, true));
+  CK(launch_iota(n_cand, d_iota, s));
+  tb = tmp_bytes;
+  CK(sort_int_keys(tmp, tb, ctx->d_pcls, d_ckey, d_iota, d_cidx, n_cand, 3, s));
+  CK(cudaMemsetAsync(d_cnt, 0, 16 * sizeof(int), s));
+  CK(launch_hist(n_cand, ctx->d_pcls, d_cnt, s));
+  int cnt[8] = {};
+  CK(cudaMemcpyAsync(cnt, d_cnt, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  {
+    EriLaunch L = base_launch(ctx);
+    int start = 0;
+    for (int pc = 0; pc < 6; ++pc) {
+      if (cnt[pc] > 0) {
+        const int cls = pc * (pc + 1) / 2 + pc;
+        L.ci = class_info_host()[cls];
+        L.diag_list = d_cidx + start;
+        L.diag_n = cnt[pc];
+        L.diag_Q = ctx->d_Q;
+        CK(eri_launch(L, cls, 1, grid_for(ctx, cls, 1, cnt[pc]), s));
+      }
+      start += cnt[pc];
+    }
+  }
+  // 4. pair Schwarz test and bins: sort by Q descending, then stably by bin
+  double* d_qmax;
+  double* d_qsorted;
+  int *d_ord, *d_bkey, *d_bkey_sorted;
+  RK(ctx->alloc(&d_qmax, 1, true));
+  RK(ctx->alloc(&d_qsorted, n_cand, true));
+  RK(ctx->alloc(&d_ord, n_cand, true));
+  RK(ctx->alloc(&d_bkey, n_cand, true));
+  RK(ctx->alloc(&d_bkey_sorted, n_cand, true));
+  RK(ctx->alloc(&ctx->d_sorted, n_cand, true));
+  tb = tmp_bytes;
+  CK(reduce_max(tmp, tb, ctx->d_Q, d_qmax, n_cand, s));
+  tb = tmp_bytes;
+  CK(sort_double_desc(tmp, tb, ctx->d_Q, d_qsorted, d_iota, d_ord, n_cand, s));
+  CK(launch_bin_keys(n_cand, ctx->d_Q, d_qmax, ctx->opt.schwarz_tau, ctx->d_pcls, d_ord, d_bkey, s));
+  tb = tmp_bytes;
+  CK(sort_int_keys(tmp, tb, d_bkey, d_bkey_sorted, d_ord, ctx->d_sorted, n_cand, 3, s));
+  CK(cudaMemsetAsync(d_cnt, 0, 16 * sizeof(int), s));
+  CK(launch_hist(n_cand, d_bkey, d_cnt, s));
+  int bins[8] = {};
+  CK(cudaMemcpyAsync(bins, d_cnt, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  RowTable rt{};
+  int acc = 0;
+  for (int b = 0; b < 6; ++b) {
+    rt.bin_start[b] = acc;
+    rt.bin_size[b] = bins[b];
+    acc += bins[b];
+  }
+  rt.bin_start[6] = acc;
+  rt.bin_size[6] = bins[6];
+  ctx->n_kept = acc;
+  RK(ctx->alloc(&ctx->d_Qs, std::max(1, acc), true));
+  CK(launch_gather_q(acc, ctx->d_sorted, ctx->d_Q, ctx->d_Qs, s));
+  // 5. quartet task rows and prefix sums
+  int rows = 0;
+  for (int cp = 0; cp < 21; ++cp) {
+    int hi = 0;
+    while ((hi + 1) * (hi + 2) / 2 <= cp) ++hi;
+    rt.row_base[cp] = rows;
+    rows += rt.bin_size[hi];
+  }
+  rt.row_base[21] = rows;
+  ctx->rt = rt;
+  ctx->n_rows = rows;
+  long long *d_rown, *d_bounds;
+  RK(ctx->alloc(&d_rown, std::max(1, rows), true));
+  RK(ctx->alloc(&ctx->d_qoff, (size_t)rows + 1, true));
+  RK(ctx->alloc(&d_bounds, 32, true));
+  CK(launch_count(rows, rt, ctx->d_Qs, ctx->opt.schwarz_tau, d_rown, s));
+  CK(cudaMemsetAsync(ctx->d_qoff, 0, sizeof(long long), s));
+  if (rows > 0) {
+    tb = tmp_bytes;
+    CK(scan_ll_inclusive(tmp, tb, d_rown, ctx->d_qoff + 1, rows, s));
+  }
+  CK(launch_gather_bounds(rt, ctx->d_qoff, d_bounds, s));
+  long long bounds[22];
+  CK(cudaMemcpyAsync(bounds, d_bounds, 22 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->ev[45], s));
+  CK(cudaStreamSynchronize(s));
+  cudaEventElapsedTime(&ctx->ms_pairs, ctx->ev[44], ctx->ev[45]);
+  long long total = 0;
+  for (int cp = 0; cp < 21; ++cp) {
+    ctx->cls_qbegin[cp] = bounds[cp];
+    ctx->cls_q[cp] = bounds[cp + 1] - bounds[cp];
+    ctx->stats.n_quartets_class[cp] = ctx->cls_q[cp];
+    total += ctx->cls_q[cp];
+  }
+  ctx->stats.n_pairs_cutoff = n_cand;
+  ctx->stats.n_pairs_kept = ctx->n_kept;
+  ctx->stats.n_quartets = total;
+  ctx->stats.ms_pairs = ctx->ms_pairs;
+  ctx->pairs_ready = true;
+  return HFX_OK;
+}
+
+extern "C" int hfx_build_K(hfx_ctx* ctx, const double* P, double* K, int ld) {
+  if (!ctx) return HFX_ERR_ARG;
+  if (!ctx->pairs_ready) return ctx->fail(HFX_ERR_STATE, "hfx_build_K before hfx_build_pairs");
+  if (!P || !K || ld < ctx->n_bf) return ctx->fail(HFX_ERR_ARG, "NULL matrix or ld < n_bf");
+  cudaStream_t s = ctx->stream;
+  const int n = ctx->n_bf;
+  if (ctx->timing) {
+    CK(cudaEventRecord(ctx->ev[0], s));
+    CK(cudaMemsetAsync(ctx->d_busy, 0, 1024 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ctx->d_counters, 0, 63 * sizeof(unsigned long long), s));
+  }
+  if (ld == n)
+    CK(cudaMemsetAsync(K, 0, sizeof(double) * (size_t)n * n, s));
+  else
+    CK(cudaMemset2DAsync(K, sizeof(double) * ld, 0, sizeof(double) * n, n, s));
+  EriLaunch L = base_launch(ctx);
+  L.sorted = ctx->d_sorted;
+  L.qoff = ctx->d_qoff;
+  L.P = P;
+  L.K = K;
+  L.ld = ld;
+  if (ctx->timing) L.busy = ctx->d_busy;
+  for (int cp = 0; cp < 21; ++cp) {
+    ctx->class_launched[cp] = false;
+    if (ctx->cls_q[cp] == 0) continue;
+    int hi = 0;
+    while ((hi + 1) * (hi + 2) / 2 <= cp) ++hi;
+    const int lo = cp - hi * (hi + 1) / 2;
+    L.ci = class_info_host()[cp];
+    L.row_begin = ctx->rt.row_base[cp];
+    L.row_end = ctx->rt.row_base[cp + 1];
+    L.bra_bin_start = ctx->rt.bin_start[hi];
+    L.ket_bin_start = ctx->rt.bin_start[lo];
+    L.q_begin = ctx->cls_qbegin[cp];
+    L.q_count = ctx->cls_q[cp];
+    L.counters = ctx->timing ? ctx->d_counters + 3 * cp : nullptr;
+    const long long items = ctx->opt.schedule == HFX_SCHED_PAIR ? (L.row_end - L.row_begin) : L.q_count;
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[2 + 2 * cp], s));
+    CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items), s));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[3 + 2 * cp], s));
+    ctx->class_launched[cp] = true;
+  }
+  CK(launch_finalize(n, ld, P, K, ctx->d_part, ctx->n_part, ctx->d_energy, s));
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
+  return HFX_OK;
+}
+
+extern "C" int hfx_build_K_host(hfx_ctx* ctx, const double* P_host, double* K_host) {
+  if (!ctx) return HFX_ERR_ARG;
+  if (!P_host || !K_host) return ctx->fail(HFX_ERR_ARG, "NULL host matrix");
+  const size_t bytes = sizeof(double) * (size_t)ctx->n_bf * ctx->n_bf;
+  if (!ctx->d_Pst) RK(ctx->alloc(&ctx->d_Pst, (size_t)ctx->n_bf * ctx->n_bf));
+  if (!ctx->d_Kst) RK(ctx->alloc(&ctx->d_Kst, (size_t)ctx->n_bf * ctx->n_bf));
+  CK(cudaMemcpyAsync(ctx->d_Pst, P_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  RK(hfx_build_K(ctx, ctx->d_Pst, ctx->d_Kst, ctx->n_bf));
+  CK(cudaMemcpyAsync(K_host, ctx->d_Kst, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HFX_OK;
+}
+
+extern "C" const double* hfx_energy_device(const hfx_ctx* ctx) { return ctx ? ctx->d_energy : nullptr; }
+
+extern "C" int hfx_energy(hfx_ctx* ctx, double* out) {
+  if (!ctx || !out) return HFX_ERR_ARG;
+  CK(cudaMemcpyAsync(out, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return HFX_OK;
+}
+
+extern "C" int hfx_set_timing(hfx_ctx* ctx, int enable) {
+  if (!ctx) return HFX_ERR_ARG;
+  ctx->timing = enable != 0;
+  return HFX_OK;
+}
+
+extern "C" int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out) {
+  if (!ctx || !out) return HFX_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  hfx_stats& st = ctx->stats;
+  for (int cp = 0; cp < 21; ++cp) st.group_size_class[cp] = eri_group_size(cp);
+  CK(cudaMemcpy(&st.energy, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost));
+  if (ctx->timing) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) st.ms_build = ms;
+    unsigned long long cnt[63];
+    CK(cudaMemcpy(cnt, ctx->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+    double fl = 0.0;
+    for (int cp = 0; cp < 21; ++cp) {
+      st.ms_class[cp] = 0.0;
+      if (ctx->class_launched[cp] && cudaEventElapsedTime(&ms, ctx->ev[2 + 2 * cp], ctx->ev[3 + 2 * cp]) == cudaSuccess)
+        st.ms_class[cp] = ms;
+      const EriClassInfo& ci = class_info_host()[cp];
+      st.prim_quartets_class[cp] = (int64_t)cnt[3 * cp];
+      st.flops_class[cp] =
+          (double)cnt[3 * cp] * (ci.flops_prim + setup_flops(ci.E, ci.F, ci.Lt, ctx->opt.omega > 0.0)) +
+          (double)cnt[3 * cp + 1] * ci.flops_quartet + (double)cnt[3 * cp + 2] * skip_flops();
+      fl += st.flops_class[cp];
+    }
+    st.flops_fp64 = fl;
+  }
+  *out = st;
+  return HFX_OK;
+}
+
+extern "C" int hfx_n_basis(const hfx_ctx* ctx) { return ctx ? ctx->n_bf : HFX_ERR_ARG; }
+
+extern "C" int64_t hfx_get_pairs(hfx_ctx* ctx, int* shell_a, int* shell_b, double* q, int64_t max_n) {
+  if (!ctx) return HFX_ERR_ARG;
+  if (!ctx->pairs_ready) return ctx->fail(HFX_ERR_STATE, "no pair list");
+  const int n = ctx->n_kept;
+  if (max_n < n || !shell_a || !shell_b || !q) return ctx->fail(HFX_ERR_ARG, "output arrays too small");
+  std::vector<int> sorted(n), sa(ctx->n_cand), sb(ctx->n_cand);
+  std::vector<double> Q(ctx->n_cand);
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(sorted.data(), ctx->d_sorted, sizeof(int) * n, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(sa.data(), ctx->d_sa, sizeof(int) * ctx->n_cand, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(sb.data(), ctx->d_sb, sizeof(int) * ctx->n_cand, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(Q.data(), ctx->d_Q, sizeof(double) * ctx->n_cand, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i) {
+    shell_a[i] = sa[sorted[i]];
+    shell_b[i] = sb[sorted[i]];
+    q[i] = Q[sorted[i]];
+  }
+  return n;
+}
+
+extern "C" int hfx_get_cta_busy(hfx_ctx* ctx, double* busy_ns, int max_n) {
+  if (!ctx || !busy_ns) return HFX_ERR_ARG;
+  const int n = std::min(max_n, ctx->n_sm);
+  std::vector<unsigned long long> b(n);
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(b.data(), ctx->d_busy, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i) busy_ns[i] = (double)b[i];
+  return n;
+}
+
+extern "C" const char* hfx_last_error(const hfx_ctx* ctx) {
+  if (!ctx) return g_init_err.c_str();
+  return ctx->err.c_str();
+}
+
+extern "C" void hfx_free(hfx_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  ctx->free_pairs();
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->ev_ok)
+    for (auto& ev : ctx->ev) cudaEventDestroy(ev);
+  delete ctx;
+}
+
+extern "C" int hfx_measure_fma_peak(double* fp64_tflops, double* fp32_tflops) {
+  if (!fp64_tflops || !fp32_tflops) return HFX_ERR_ARG;
+  cudaError_t e = fma_peak(fp64_tflops, fp32_tflops);
+  if (e != cudaSuccess) {
+    g_init_err = std::string("fma probe: ") + cudaGetErrorString(e);
+    return HFX_ERR_CUDA;
+  }
+  return HFX_OK;
+}

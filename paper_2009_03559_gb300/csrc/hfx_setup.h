@@ -1,0 +1,49 @@
+// Host wrappers of the set-up / finalisation kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include "hfx_internal.cuh"
+
+namespace hfx {
+
+// Rows of the quartet task list: class pair cp = hi(hi+1)/2 + lo owns rows
+// [row_base[cp], row_base[cp+1]), one per bra pair of bin hi.
+struct RowTable {
+  int row_base[22];
+  int bin_start[7];
+  int bin_size[7];
+};
+
+cudaError_t launch_normalize(int n_shells, const int* l, const int* nprim, const int* prim_off,
+                             const double* alpha, const double* coef, double* w, cudaStream_t s);
+cudaError_t launch_boys_table(double* tab, cudaStream_t s);
+cudaError_t launch_pair_flags(long long n_tri, const int* atom, const double* xyz, double rcut, int* flag,
+                              cudaStream_t s);
+cudaError_t select_flagged(void* tmp, size_t& tmp_bytes, long long n_tri, const int* flag, long long* out,
+                           int* d_num, cudaStream_t s);
+cudaError_t launch_pair_setup(int n_cand, const long long* cand_t, const int* l, const int* nprim,
+                              const int* atom, const double* xyz, int* sa, int* sb, int* pcls, double* AB,
+                              int* cap, cudaStream_t s);
+cudaError_t scan_int(void* tmp, size_t& tmp_bytes, const int* in, int* out, int n, cudaStream_t s);
+cudaError_t scan_ll_inclusive(void* tmp, size_t& tmp_bytes, const long long* in, long long* out, int n,
+                              cudaStream_t s);
+cudaError_t launch_prim_fill(int n_cand, const int* sa, const int* sb, const int* nprim, const int* prim_off_shell,
+                             const int* atom, const double* xyz, const double* alpha, const double* w,
+                             const int* pp_off, double prim_tau, PrimPair* pp, int* pp_n, cudaStream_t s);
+cudaError_t launch_iota(int n, int* v, cudaStream_t s);
+cudaError_t launch_hist(int n, const int* key, int* counts, cudaStream_t s);
+cudaError_t sort_int_keys(void* tmp, size_t& tmp_bytes, const int* kin, int* kout, const int* vin, int* vout,
+                          int n, int end_bit, cudaStream_t s);
+cudaError_t sort_double_desc(void* tmp, size_t& tmp_bytes, const double* kin, double* kout, const int* vin,
+                             int* vout, int n, cudaStream_t s);
+cudaError_t reduce_max(void* tmp, size_t& tmp_bytes, const double* in, double* out, int n, cudaStream_t s);
+cudaError_t launch_bin_keys(int n, const double* Q, const double* qmax, double tau, const int* pcls,
+                            const int* order, int* binkey, cudaStream_t s);
+cudaError_t launch_gather_q(int n, const int* sorted, const double* Q, double* Qs, cudaStream_t s);
+cudaError_t launch_count(int n_rows, const RowTable& rt, const double* Qs, double tau, long long* row_n,
+                         cudaStream_t s);
+cudaError_t launch_gather_bounds(const RowTable& rt, const long long* qoff, long long* out, cudaStream_t s);
+cudaError_t launch_finalize(int n, int ld, const double* P, double* K, double* part, int n_part, double* energy,
+                            cudaStream_t s);
+cudaError_t fma_peak(double* fp64_tflops, double* fp32_tflops);
+
+}  // namespace hfx

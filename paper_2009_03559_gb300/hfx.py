@@ -1,0 +1,236 @@
+"""Python binding of the C ABI in include/hfx.h (argument marshalling only).
+
+Every step of the exchange build runs in the CUDA library ``_build/libhfx.so``; this
+module loads it with ctypes and passes pointers.  There is no CPU path: if the library
+or a CUDA device is missing, constructing ``HFX`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhfx.so")
+
+HFX_FP64, HFX_MIXED = 0, 1
+HFX_SCHED_QUARTET, HFX_SCHED_PAIR = 0, 1
+ERR_NAMES = {0: "OK", -1: "ARG", -2: "UNSUPPORTED_L", -3: "OOM", -4: "CUDA", -5: "STATE", -6: "TIMEOUT"}
+
+PAIR_CLASSES = ["ss", "ps", "pp", "ds", "dp", "dd"]
+QUARTET_CLASSES = [f"({PAIR_CLASSES[hi]}|{PAIR_CLASSES[lo]})" for hi in range(6) for lo in range(hi + 1)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("schwarz_tau", ctypes.c_double), ("rcut_bohr", ctypes.c_double),
+                ("prim_tau", ctypes.c_double), ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_pairs_cutoff", ctypes.c_int64), ("n_pairs_kept", ctypes.c_int64),
+                ("n_quartets", ctypes.c_int64), ("n_quartets_class", ctypes.c_int64 * 21),
+                ("prim_quartets_class", ctypes.c_int64 * 21),
+                ("flops_fp64", ctypes.c_double), ("flops_class", ctypes.c_double * 21),
+                ("group_size_class", ctypes.c_int32 * 21),
+                ("ms_pairs", ctypes.c_double), ("ms_build", ctypes.c_double),
+                ("ms_class", ctypes.c_double * 21), ("energy", ctypes.c_double)]
+
+    def as_dict(self):
+        return {
+            "n_pairs_cutoff": int(self.n_pairs_cutoff), "n_pairs_kept": int(self.n_pairs_kept),
+            "n_quartets": int(self.n_quartets), "n_quartets_class": [int(x) for x in self.n_quartets_class],
+            "prim_quartets_class": [int(x) for x in self.prim_quartets_class],
+            "flops_fp64": float(self.flops_fp64), "flops_class": [float(x) for x in self.flops_class],
+            "group_size_class": [int(x) for x in self.group_size_class], "ms_pairs": float(self.ms_pairs),
+            "ms_build": float(self.ms_build), "ms_class": [float(x) for x in self.ms_class],
+            "energy": float(self.energy),
+        }
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhfx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    L.hfx_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.hfx_default_options.restype = None
+    L.hfx_init_basis.argtypes = [ctypes.POINTER(vp), ctypes.c_int, dp, ctypes.c_int, ip, ip, ip, dp, dp,
+                                 ctypes.POINTER(Options), vp]
+    L.hfx_init_basis.restype = ctypes.c_int
+    L.hfx_build_pairs.argtypes = [vp]
+    L.hfx_build_pairs.restype = ctypes.c_int
+    L.hfx_build_K.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.hfx_build_K.restype = ctypes.c_int
+    L.hfx_build_K_host.argtypes = [vp, dp, dp]
+    L.hfx_build_K_host.restype = ctypes.c_int
+    L.hfx_energy_device.argtypes = [vp]
+    L.hfx_energy_device.restype = vp
+    L.hfx_energy.argtypes = [vp, dp]
+    L.hfx_energy.restype = ctypes.c_int
+    L.hfx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.hfx_get_stats.restype = ctypes.c_int
+    L.hfx_set_timing.argtypes = [vp, ctypes.c_int]
+    L.hfx_set_timing.restype = ctypes.c_int
+    L.hfx_n_basis.argtypes = [vp]
+    L.hfx_n_basis.restype = ctypes.c_int
+    L.hfx_get_pairs.argtypes = [vp, ip, ip, dp, ctypes.c_int64]
+    L.hfx_get_pairs.restype = ctypes.c_int64
+    L.hfx_get_cta_busy.argtypes = [vp, dp, ctypes.c_int]
+    L.hfx_get_cta_busy.restype = ctypes.c_int
+    L.hfx_last_error.argtypes = [vp]
+    L.hfx_last_error.restype = ctypes.c_char_p
+    L.hfx_free.argtypes = [vp]
+    L.hfx_free.restype = None
+    L.hfx_measure_fma_peak.argtypes = [dp, dp]
+    L.hfx_measure_fma_peak.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class HFXError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hfx error {code} ({ERR_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def default_options() -> Options:
+    o = Options()
+    load_library().hfx_default_options(ctypes.byref(o))
+    return o
+
+
+def measure_fma_peak():
+    """(FP64 TFLOP/s, FP32 TFLOP/s) of the current device from an FMA-chain kernel."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    L = load_library()
+    rc = L.hfx_measure_fma_peak(ctypes.byref(a), ctypes.byref(b))
+    if rc != 0:
+        raise HFXError(rc, L.hfx_last_error(None).decode())
+    return a.value, b.value
+
+
+class HFX:
+    """One system: basis on the device, pair list, K builds.
+
+    ``system`` is an ``inputs.System``; ``stream`` a torch.cuda.Stream (or None for the
+    current stream).  ``build_K(P)`` takes and returns torch CUDA float64 tensors.
+    """
+
+    def __init__(self, system, stream=None, tau=None, rcut=None, omega=None, schedule=HFX_SCHED_QUARTET,
+                 prim_tau=None):
+        import torch  # device memory and streams only
+        if not torch.cuda.is_available():
+            raise RuntimeError("HFX needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        L = load_library()
+        self.L = L
+        self.system = system
+        o = default_options()
+        o.omega = system.omega if omega is None else omega
+        o.schwarz_tau = system.tau if tau is None else tau
+        o.rcut_bohr = system.rcut if rcut is None else rcut
+        if prim_tau is not None:
+            o.prim_tau = prim_tau
+        o.schedule = schedule
+        self.options = o
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        xyz, sa, sl, sn, al, co = system.basis_arrays()
+        self._host = (xyz, sa, sl, sn, al, co)
+        h = ctypes.c_void_p()
+        rc = L.hfx_init_basis(ctypes.byref(h), int(xyz.shape[0]), _dp(xyz), int(sl.shape[0]), _ip(sa), _ip(sl),
+                              _ip(sn), _dp(al), _dp(co), ctypes.byref(o), ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise HFXError(rc, L.hfx_last_error(None).decode())
+        self.h = h
+        self.n_bf = L.hfx_n_basis(h)
+        self.pairs_built = False
+
+    def _check(self, rc):
+        if rc != 0:
+            raise HFXError(rc, self.L.hfx_last_error(self.h).decode())
+
+    def build_pairs(self):
+        self._check(self.L.hfx_build_pairs(self.h))
+        self.pairs_built = True
+        return self
+
+    def set_timing(self, on=True):
+        self._check(self.L.hfx_set_timing(self.h, 1 if on else 0))
+
+    def build_K(self, P, K=None):
+        """K for the density P (torch float64 CUDA tensor, n x n, contiguous rows)."""
+        torch = self.torch
+        n = self.n_bf
+        if not (P.is_cuda and P.dtype == torch.float64 and P.shape == (n, n) and P.stride(1) == 1):
+            raise ValueError("P must be a float64 CUDA tensor of shape (n_bf, n_bf) with unit column stride")
+        if K is None:
+            K = torch.empty((n, n), dtype=torch.float64, device=P.device)
+        ld = P.stride(0)
+        if K.stride(0) != ld or K.stride(1) != 1:
+            raise ValueError("K must have the same row stride as P")
+        self._check(self.L.hfx_build_K(self.h, ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(K.data_ptr()), ld))
+        return K
+
+    def build_K_host(self, P: np.ndarray) -> np.ndarray:
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        assert P.shape == (self.n_bf, self.n_bf)
+        K = np.empty_like(P)
+        self._check(self.L.hfx_build_K_host(self.h, _dp(P), _dp(K)))
+        return K
+
+    def energy(self) -> float:
+        e = ctypes.c_double()
+        self._check(self.L.hfx_energy(self.h, ctypes.byref(e)))
+        return e.value
+
+    def energy_device_ptr(self) -> int:
+        return int(self.L.hfx_energy_device(self.h))
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self.L.hfx_get_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def pairs(self):
+        n = self.stats()["n_pairs_kept"]
+        a = np.zeros(max(n, 1), np.int32)
+        b = np.zeros(max(n, 1), np.int32)
+        q = np.zeros(max(n, 1))
+        r = self.L.hfx_get_pairs(self.h, _ip(a), _ip(b), _dp(q), int(max(n, 1)))
+        if r < 0:
+            raise HFXError(int(r), self.L.hfx_last_error(self.h).decode())
+        return a[:r], b[:r], q[:r]
+
+    def sm_busy_ns(self, max_n=1024):
+        out = np.zeros(max_n)
+        r = self.L.hfx_get_cta_busy(self.h, _dp(out), max_n)
+        self._check(0 if r >= 0 else r)
+        return out[:r]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.hfx_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
