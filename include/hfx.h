@@ -158,6 +158,24 @@ const char* hfx_last_error(const hfx_ctx* ctx);
 /* Releases the context and all device memory it owns (synchronises the stream). */
 void hfx_free(hfx_ctx* ctx);
 
+/* Largest matrix order accepted by hfx_energy_noalloc (rows of its fixed scratch). */
+#define HFX_NOALLOC_MAX_N 16384
+
+/* E = sum_{mu nu} P_{mu nu} K_{mu nu} for device matrices P and K (n x n, leading
+ * dimension ld), written to the device scalar *E_dev, with NO device allocation: for
+ * callers that cannot let a library call cudaMalloc (programs that serve all device
+ * memory from their own pool or under a fixed budget, or loops where an allocation
+ * would synchronise the device).  The paper has no counterpart of this entry point.
+ * Scratch: a fixed library-resident device array of 2 * HFX_NOALLOC_MAX_N doubles
+ * (256 KiB) on every device that loads the library, kept until process exit.  The
+ * first call on a device looks up that array's address (make it before any stream
+ * capture).  Calls share the array: calls that overlap on the GPU race, so order them
+ * (e.g. one stream).  Each call writes all scratch it reads; nothing needs clearing.
+ * Work is queued on `stream` (cudaStream_t, NULL = default).  Errors: HFX_ERR_ARG for
+ * NULL pointers, n < 1, n > HFX_NOALLOC_MAX_N or ld < n (message via
+ * hfx_last_error(NULL)); HFX_ERR_CUDA if the address lookup or a launch fails. */
+int hfx_energy_noalloc(const double* P_dev, const double* K_dev, int n, int ld, double* E_dev, void* stream);
+
 /* Measures the FP64 and FP32 fused-multiply-add throughput of the current device with
  * a register-resident FMA chain (TFLOP/s, FMA = 2 flops).  Used as the roofline
  * denominators for the FP64/FP32 ALU-bound kernels. */

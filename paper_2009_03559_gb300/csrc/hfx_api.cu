@@ -74,6 +74,11 @@ struct hfx_ctx {
 
 static thread_local std::string g_init_err;
 
+namespace hfx {
+// message for hfx_last_error(NULL) from entry points that have no context
+void set_global_error(const std::string& msg) { g_init_err = msg; }
+}  // namespace hfx
+
 #define CK(call)                                        \
   do {                                                  \
     cudaError_t e_ = (call);                            \

@@ -90,6 +90,8 @@ def load_library(path: str = LIB_PATH):
     L.hfx_last_error.restype = ctypes.c_char_p
     L.hfx_free.argtypes = [vp]
     L.hfx_free.restype = None
+    L.hfx_energy_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    L.hfx_energy_noalloc.restype = ctypes.c_int
     L.hfx_measure_fma_peak.argtypes = [dp, dp]
     L.hfx_measure_fma_peak.restype = ctypes.c_int
     _lib = L
