@@ -31,6 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "HFX K-build ms & screened ERI quartets/s vs plain FP64; p50/p99 latency"
+def workload_desc(s):
+    return (f"diamond-{s.n_atoms} DZP-like: {s.n_atoms} atoms (a=10.26 bohr cells), {s.n_shells} shells "
+            f"s,s,p,p,d, {s.n_bf} spherical functions, 3 primitives/shell, omega=0.11, r_c=6 bohr, "
+            f"tau=1e-8, P truncated beyond 10 bohr; plain FP64")
+
+
 WORKLOAD = ("diamond-64 DZP-like: 64 atoms (2x2x2 cells, a=10.26 bohr), 320 shells s,s,p,p,d, "
             "832 spherical functions, 3 primitives/shell, omega=0.11, r_c=6 bohr, tau=1e-8, "
             "P truncated beyond 10 bohr; plain FP64")
@@ -167,6 +173,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-sample", type=int, default=60000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--atoms", type=int, default=64,
+                    help="diamond piece size (64 = the benchmark workload; smaller for profiler captures)")
+    ap.add_argument("--report", action="store_true", help="per-class table on stderr")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_info()
@@ -186,7 +196,7 @@ def main():
         torch.cuda.set_device(0)
     from paper_2009_03559_gb300 import hfx, inputs
 
-    s, P_np = inputs.config1(64)
+    s, P_np = inputs.config1(args.atoms)
     stream = torch.cuda.Stream()
     h = hfx.HFX(s, stream=stream)
     h.build_pairs()
@@ -231,7 +241,7 @@ def main():
 
     # end-to-end through the host-buffer entry point (copies inside the timed region)
     e2e_t = []
-    for i in range(max(2, min(args.steps, 3))):
+    for i in range(args.e2e_steps):
         t0 = time.perf_counter()
         Kh = h.build_K_host(P_np)
         e2e_t.append(time.perf_counter() - t0)
@@ -257,10 +267,10 @@ def main():
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_bf": s.n_bf, "quartets_per_step": n_q,
+            "config": {"workload": workload_desc(s), "n_bf": s.n_bf, "quartets_per_step": n_q,
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{ws}",
                        "energy_E_K": energy},
-            "e2e": {"value": n_q / float(np.median(e2e_t)), "unit": "quartets/s",
+            "e2e": {"value": n_q / float(np.median(e2e_t)) if e2e_t else None, "unit": "quartets/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "alu", "kernel": "eri_g32_kernel (FP64 classes with warp groups)",
@@ -273,6 +283,16 @@ def main():
             "fp32_peak_tflops": fp32_peak,
             "class_ms": {QUARTET_CLASSES[c]: round(ms_cls[c], 3) for c in range(21)},
         }
+        if args.report:
+            print(f"{'class':9s} {'G':>2s} {'quartets':>11s} {'prims':>12s} {'ms':>9s} {'TF/s':>6s} {'frac':>5s}",
+                  file=sys.stderr)
+            for c in range(21):
+                ms = ms_cls[c]
+                fl = flops_cls[c]
+                tf = fl / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+                print(f"{QUARTET_CLASSES[c]:9s} {st_timed['group_size_class'][c]:2d} "
+                      f"{st_timed['n_quartets_class'][c]:11d} {st_timed['prim_quartets_class'][c]:12d} "
+                      f"{ms:9.2f} {tf:6.3f} {tf / fp64_peak:5.2f}", file=sys.stderr)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(line), flush=True)
