@@ -56,8 +56,10 @@ extern "C" {
 #define HFX_MIXED 1               /* small-bound s,p quartets in FP32, see hfx_options */
 
 /* work schedules inside a class launch (paper Sec. 3.2, Algorithms 2 and 3) */
-#define HFX_SCHED_QUARTET 0       /* even split of the screened quartet list (default) */
-#define HFX_SCHED_PAIR 1          /* even split of the bra pair list, screening after */
+#define HFX_SCHED_QUARTET 0       /* static even split of the screened quartet list */
+#define HFX_SCHED_PAIR 1          /* static even split of the bra pair list, screening after */
+#define HFX_SCHED_DYNAMIC 2       /* chunks of the quartet list handed out by a device atomic
+                                     counter (the paper's "dynamic distribution"; default) */
 
 typedef struct hfx_ctx hfx_ctx;   /* opaque, library-owned */
 
@@ -67,8 +69,10 @@ typedef struct {
   double rcut_bohr;    /* orbital cutoff radius r_c; <= 0 disables the pair-distance screen */
   double prim_tau;     /* primitive pairs with |prefactor| below this are dropped (default 1e-22) */
   int precision;       /* HFX_FP64 (only mode of this version) */
-  int schedule;        /* HFX_SCHED_QUARTET or HFX_SCHED_PAIR */
-  int reserved[6];     /* set to 0 */
+  int schedule;        /* HFX_SCHED_DYNAMIC (default), HFX_SCHED_QUARTET or HFX_SCHED_PAIR */
+  int skip_zero_p;     /* 1 (default): skip quartets whose four density blocks P_bd, P_bc,
+                          P_ad, P_ac are all exactly zero (their contribution is exactly 0) */
+  int reserved[5];     /* set to 0 */
 } hfx_options;
 
 typedef struct {
@@ -78,6 +82,8 @@ typedef struct {
   int64_t n_quartets_class[21];/* per class, index hi*(hi+1)/2 + lo over pair classes
                                   ss, ps, pp, ds, dp, dd */
   int64_t prim_quartets_class[21]; /* primitive quartets evaluated per class (timed builds) */
+  int64_t quartets_evaluated_class[21]; /* quartets evaluated per class (timed builds): the kept
+                                  quartets minus those skipped for exactly-zero density blocks */
   double flops_fp64;           /* FP64 flops of the last timed K build (operation-count model
                                   of the kernels: add/mul = 1, fma = 2) */
   double flops_class[21];      /* the same per class */
@@ -89,7 +95,7 @@ typedef struct {
 } hfx_stats;
 
 /* Fills *opt with defaults: omega 0.11, tau 1e-10, no cutoff, prim_tau 1e-22, FP64,
- * quartet schedule. */
+ * dynamic schedule, zero-density-block skip on. */
 void hfx_default_options(hfx_options* opt);
 
 /* Creates a context for one system and uploads its basis.

@@ -49,22 +49,26 @@ def _newest(paths) -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False,
+          extra_flags=(), out_dir: str = BUILD) -> str:
+    """Compile into out_dir/libhfx.so; extra_flags (e.g. -D tuning macros) go to nvcc."""
+    lib_path = os.path.join(out_dir, "libhfx.so")
+    os.makedirs(out_dir, exist_ok=True)
     if not _tables_current():
         generate_tables()
     deps = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "hfx.h"), __file__]
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest(deps + srcs):
-        return LIB
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= _newest(deps + srcs):
+        return lib_path
     nv = nvcc()
     flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
              "--expt-relaxed-constexpr"]
     if ptxas_verbose:
         flags += ["-Xptxas", "-v"]
+    flags += list(extra_flags)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(out_dir, os.path.basename(src).replace(".cu", ".o"))
         cmd = [nv] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -78,13 +82,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if err:
                 print(err, file=sys.stderr)
     objs = [o for o, _ in results]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nv, ARCH, "-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -140,29 +140,44 @@ __device__ __forceinline__ void store_coef(const CoefRg& c, const double* Gm, in
     if (m <= Lt) cf[CF_G + m] = Gm[m];
 }
 
-// One bra VRR op: V[dst] = PA_i V[s1] + WP_i V[s2] (+ n/(2p) (V[s3] - rho/p V[s4])).
-template <class Coef>
-__device__ __forceinline__ void vrr_bra(uint4 op, double* V, int st, const Coef& c) {
-  const int dst = op.x & 0xFFFF, s1 = op.x >> 16, s2 = op.y & 0xFFFF, s3 = op.y >> 16, s4 = op.z & 0xFFFF;
-  const int i = op.w & 3, nA = (op.w >> 2) & 7;
-  double v = c.pa(i) * V[s1 * st];
-  v = fma(c.wp(i), V[s2 * st], v);
-  if (nA) v = fma(c.ca(nA), fma(-c.rp(), V[s4 * st], V[s3 * st]), v);
-  V[dst * st] = v;
+__device__ __forceinline__ uint4 ld_op(const uint32_t* base, int idx) {
+  return __ldg(reinterpret_cast<const uint4*>(base) + idx);
 }
 
-// One ket VRR op: V[dst] = QC_i V[s1] + WQ_i V[s2] (+ n/(2q) (V[s3] - rho/q V[s4]))
-//                          (+ e_i/(2(p+q)) V[s5]).
-template <class Coef>
-__device__ __forceinline__ void vrr_ket(uint4 op, double* V, int st, const Coef& c) {
+// VRR ops.  bra:  v = PA_i V[s1] + WP_i V[s2] (+ n/(2p) (V[s3] - rho/p V[s4]))
+//           ket:  v = QC_i V[s1] + WQ_i V[s2] (+ n/(2q) (V[s3] - rho/q V[s4]))
+//                                             (+ e_i/(2(p+q)) V[s5])
+// The result is stored to V[dst]; ops flagged "acc" (targets no op reads) instead add it
+// to the accumulator S[dst], starting their FMA chain from the accumulator value.
+// FOLD = false compiles the plain form (no accumulator branch) for classes without folding.
+template <bool FOLD, class Coef>
+__device__ __forceinline__ void vrr_bra(uint4 op, double* V, double* S, int st, const Coef& c) {
+  const int dst = op.x & 0xFFFF, s1 = op.x >> 16, s2 = op.y & 0xFFFF, s3 = op.y >> 16, s4 = op.z & 0xFFFF;
+  const int i = op.w & 3, nA = (op.w >> 2) & 7;
+  const bool acc = FOLD && ((op.w >> 8) & 1);
+  double v = acc ? fma(c.pa(i), V[s1 * st], S[dst * st]) : c.pa(i) * V[s1 * st];
+  v = fma(c.wp(i), V[s2 * st], v);
+  if (nA) v = fma(c.ca(nA), fma(-c.rp(), V[s4 * st], V[s3 * st]), v);
+  if (acc)
+    S[dst * st] = v;
+  else
+    V[dst * st] = v;
+}
+
+template <bool FOLD, class Coef>
+__device__ __forceinline__ void vrr_ket(uint4 op, double* V, double* S, int st, const Coef& c) {
   const int dst = op.x & 0xFFFF, s1 = op.x >> 16, s2 = op.y & 0xFFFF, s3 = op.y >> 16;
   const int s4 = op.z & 0xFFFF, s5 = op.z >> 16;
   const int i = op.w & 3, nA = (op.w >> 2) & 7, nB = (op.w >> 5) & 7;
-  double v = c.qc(i) * V[s1 * st];
+  const bool acc = FOLD && ((op.w >> 8) & 1);
+  double v = acc ? fma(c.qc(i), V[s1 * st], S[dst * st]) : c.qc(i) * V[s1 * st];
   v = fma(c.wq(i), V[s2 * st], v);
   if (nA) v = fma(c.ck(nA), fma(-c.rq(), V[s4 * st], V[s3 * st]), v);
   if (nB) v = fma(c.cb(nB), V[s5 * st], v);
-  V[dst * st] = v;
+  if (acc)
+    S[dst * st] = v;
+  else
+    V[dst * st] = v;
 }
 
 // Post-contraction op on the group scratch S.
@@ -181,10 +196,6 @@ __device__ __forceinline__ void post_op(uint4 op, int type, double* S, int st, c
     v = fma(d, S[s2 * st], S[s1 * st]);
   }
   S[dst * st] = v;
-}
-
-__device__ __forceinline__ uint4 ld_op(const uint32_t* base, int idx) {
-  return __ldg(reinterpret_cast<const uint4*>(base) + idx);
 }
 
 // Digest of the final spherical block v (stride st) into the half matrix A.

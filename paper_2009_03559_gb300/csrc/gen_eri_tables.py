@@ -30,6 +30,11 @@ import math
 import sys
 
 PAIR_CLASSES = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+FOLD = "--no-fold" not in sys.argv
+# classes whose group scratch fits in this many doubles run one quartet per thread
+# (the kernels read this limit from the generated header); only those fold their
+# accumulation into the VRR ops, which measured faster there and slower for warp groups
+G1_MAX_SCRATCH = 100
 
 
 def monos(l):
@@ -95,7 +100,12 @@ class ClassTables:
         self.la, self.lb, self.lc, self.ld = la, lb, lc, ld
         self.E, self.F = la + lb, lc + ld
         self.Lt = self.E + self.F
+        self.fold = False
         self.build()
+        T, _ = self.layout()
+        if FOLD and T <= G1_MAX_SCRATCH:   # folding leaves the layout unchanged
+            self.fold = True
+            self.build()
 
     # ------------------------------------------------------------------ VRR
     def build(self):
@@ -193,10 +203,30 @@ class ClassTables:
         self.e_list = [e for de in range(la, E + 1) for e in monos(de)]
         self.f_list = [f for df in range(lc, F + 1) for f in monos(df)]
         self.n_acc = len(self.e_list) * len(self.f_list)
-        self.acc_src = []
-        for ie, e in enumerate(self.e_list):
-            for jf, f in enumerate(self.f_list):
-                self.acc_src.append(slot[(e, f, 0)])
+        # contraction: a target that no op reads is accumulated by the op that makes it
+        # (the op ends its FMA chain on the accumulator: one FP64 add saved per target);
+        # the others are added from their slot after the last level
+        read = set()
+        for lvl in self.bra_ops + self.ket_ops:
+            for o in lvl:
+                read.update(o["s"][:2])
+                if o["nA"]:
+                    read.update(o["s"][2:4])
+                if o["nB"]:
+                    read.add(o["s"][4])
+        writer = {o["dst"]: o for lvl in self.bra_ops + self.ket_ops for o in lvl}
+        self.acc_src = []      # (acc index, slot) added after the levels
+        self.n_folded = 0
+        a = 0
+        for e in self.e_list:
+            for f in self.f_list:
+                sl = slot[(e, f, 0)]
+                if self.fold and sl in writer and sl not in read:
+                    writer[sl]["acc"] = a
+                    self.n_folded += 1
+                else:
+                    self.acc_src.append((a, sl))
+                a += 1
         self.build_hrr()
 
     # ------------------------------------------------------------------ HRR + sph
@@ -360,7 +390,7 @@ class ClassTables:
         for lvl in self.ket_ops:
             for o in lvl:
                 vrr += 3 + (4 if o["nA"] else 0) + (2 if o["nB"] else 0)
-        acc = self.n_acc
+        acc = self.n_acc - self.n_folded
         hrr = sph = 0
         for st in self.stages:
             for _, srcs, _ in st["ops"]:
@@ -391,12 +421,16 @@ class ClassTables:
 
 
 def pack_vrr(o):
-    """uint4 op: dst|s1, s2|s3, s4|s5 (16 bits each), dir | nA << 2 | nB << 5."""
+    """uint4 op: dst|s1, s2|s3, s4|s5 (16 bits each), dir | nA << 2 | nB << 5 | acc << 8.
+    With the acc flag, dst is an accumulator index (group scratch slot) and the op adds
+    its value there instead of storing a VRR slot."""
     s = o["s"]
-    return [(o["dst"] & 0xFFFF) | ((s[0] & 0xFFFF) << 16),
+    acc = "acc" in o
+    dst = o["acc"] if acc else o["dst"]
+    return [(dst & 0xFFFF) | ((s[0] & 0xFFFF) << 16),
             (s[1] & 0xFFFF) | ((s[2] & 0xFFFF) << 16),
             (s[3] & 0xFFFF) | ((s[4] & 0xFFFF) << 16),
-            o["dir"] | (o["nA"] << 2) | (o["nB"] << 5)]
+            o["dir"] | (o["nA"] << 2) | (o["nB"] << 5) | (int(acc) << 8)]
 
 
 def all_classes():
@@ -429,7 +463,7 @@ def emit(classes, f=sys.stdout):
             for o in lvl:
                 vrr_words.extend(pack_vrr(o))
         acc_off = len(acc_words)
-        acc_words.extend(c.acc_src)
+        acc_words.extend([(a & 0xFFFF) | ((sl & 0xFFFF) << 16) for a, sl in c.acc_src])
         p_type, p_off, p_n = [], [], []
         for k, st in enumerate(c.stages):
             src_base = bases[k]
@@ -458,7 +492,8 @@ def emit(classes, f=sys.stdout):
             w("  " + ", ".join(f"{x}u" for x in ws[i:i + per_line]) + ",\n")
         w("};\n\n")
 
-    w(f"#define HFX_N_CLASSES {len(classes)}\n\n")
+    w(f"#define HFX_N_CLASSES {len(classes)}\n")
+    w(f"#define HFX_G1_MAX_SCRATCH {G1_MAX_SCRATCH}\n\n")
     w("static const double kSphCoefHost[6] = {" + ", ".join(repr(x) for x in SPH_COEF) + "};\n\n")
     arr("kVrrOps", vrr_words)
     arr("kPostOps", post_words)
@@ -477,7 +512,7 @@ def emit(classes, f=sys.stdout):
             str(c.la), str(c.lb), str(c.lc), str(c.ld), str(c.E), str(c.F), str(c.Lt),
             str(c.n_acc), str(r["work_base"]), str(r["T"]),
             str(len(c.bra_ops)), str(len(c.ket_ops)),
-            lst(r["lv_off"], 8), lst(r["lv_n"], 8), str(r["acc_off"]),
+            lst(r["lv_off"], 8), lst(r["lv_n"], 8), str(r["acc_off"]), str(len(c.acc_src)),
             str(len(c.stages)), lst(r["p_type"], 8), lst(r["p_off"], 8), lst(r["p_n"], 8),
             str(r["out_base"]), lst(c.final_dims, 4),
             str(fl["vrr"] + fl["acc"]), str(fl["hrr"] + fl["sph"] + fl["digest"]),

@@ -34,11 +34,12 @@ struct hfx_ctx {
   long long cls_q[21] = {}, cls_qbegin[21] = {};
   bool pairs_ready = false;
   // per build
-  double *d_energy = nullptr, *d_part = nullptr;
+  double *d_energy = nullptr, *d_part = nullptr, *d_pmax = nullptr;
   int n_part = 0;
   double *d_Pst = nullptr, *d_Kst = nullptr;
   unsigned long long* d_busy = nullptr;      // per SM
   unsigned long long* d_counters = nullptr;  // 3 per class
+  unsigned long long* d_work = nullptr;      // dynamic-schedule claim counter per class
   bool timing = false;
   cudaEvent_t ev[2 * 21 + 4] = {};
   bool ev_ok = false;
@@ -98,7 +99,8 @@ extern "C" void hfx_default_options(hfx_options* opt) {
   opt->rcut_bohr = 0.0;
   opt->prim_tau = 1e-22;
   opt->precision = HFX_FP64;
-  opt->schedule = HFX_SCHED_QUARTET;
+  opt->schedule = HFX_SCHED_DYNAMIC;
+  opt->skip_zero_p = 1;
 }
 
 extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int n_shells,
@@ -118,7 +120,7 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
   hfx_default_options(&o);
   if (opt) o = *opt;
   if (!(o.omega >= 0.0) || !(o.schwarz_tau >= 0.0) || !(o.prim_tau >= 0.0) || o.precision != HFX_FP64 ||
-      (o.schedule != HFX_SCHED_QUARTET && o.schedule != HFX_SCHED_PAIR)) {
+      (o.schedule != HFX_SCHED_QUARTET && o.schedule != HFX_SCHED_PAIR && o.schedule != HFX_SCHED_DYNAMIC)) {
     g_init_err = "invalid options";
     return HFX_ERR_ARG;
   }
@@ -176,7 +178,8 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
       (r = ctx->alloc(&ctx->d_l, n_shells)) || (r = ctx->alloc(&ctx->d_nprim, n_shells)) ||
       (r = ctx->alloc(&ctx->d_prim_off, n_shells)) || (r = ctx->alloc(&ctx->d_bf_off, n_shells)) ||
       (r = ctx->alloc(&ctx->d_energy, 1)) || (r = ctx->alloc(&ctx->d_busy, 1024)) ||
-      (r = ctx->alloc(&ctx->d_counters, 3 * 21)))
+      (r = ctx->alloc(&ctx->d_counters, 3 * 21)) ||
+      (r = ctx->alloc(&ctx->d_pmax, (size_t)n_shells * n_shells)) || (r = ctx->alloc(&ctx->d_work, 32)))
     return bail(r);
   ctx->n_part = 2 * ctx->n_sm;
   if ((r = ctx->alloc(&ctx->d_part, 2 * (size_t)ctx->n_part))) return bail(r);
@@ -435,6 +438,12 @@ extern "C" int hfx_build_K(hfx_ctx* ctx, const double* P, double* K, int ld) {
   L.P = P;
   L.K = K;
   L.ld = ld;
+  if (ctx->opt.schedule == HFX_SCHED_DYNAMIC) CK(cudaMemsetAsync(ctx->d_work, 0, 32 * sizeof(unsigned long long), s));
+  if (ctx->opt.skip_zero_p) {
+    CK(launch_pmax(ctx->n_shells, ctx->d_bf_off, ctx->d_l, P, ld, ctx->d_pmax, s));
+    L.pmax = ctx->d_pmax;
+    L.ns = ctx->n_shells;
+  }
   if (ctx->timing) L.busy = ctx->d_busy;
   for (int cp = 0; cp < 21; ++cp) {
     ctx->class_launched[cp] = false;
@@ -450,6 +459,8 @@ extern "C" int hfx_build_K(hfx_ctx* ctx, const double* P, double* K, int ld) {
     L.q_begin = ctx->cls_qbegin[cp];
     L.q_count = ctx->cls_q[cp];
     L.counters = ctx->timing ? ctx->d_counters + 3 * cp : nullptr;
+    L.work = ctx->d_work + cp;
+    L.chunk = eri_group_size(cp) == 1 ? 256 : 8;
     const long long items = ctx->opt.schedule == HFX_SCHED_PAIR ? (L.row_end - L.row_begin) : L.q_count;
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[2 + 2 * cp], s));
     CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items), s));
@@ -507,6 +518,7 @@ extern "C" int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out) {
         st.ms_class[cp] = ms;
       const EriClassInfo& ci = class_info_host()[cp];
       st.prim_quartets_class[cp] = (int64_t)cnt[3 * cp];
+      st.quartets_evaluated_class[cp] = (int64_t)cnt[3 * cp + 1];
       st.flops_class[cp] =
           (double)cnt[3 * cp] * (ci.flops_prim + setup_flops(ci.E, ci.F, ci.Lt, ctx->opt.omega > 0.0)) +
           (double)cnt[3 * cp + 1] * ci.flops_quartet + (double)cnt[3 * cp + 2] * skip_flops();

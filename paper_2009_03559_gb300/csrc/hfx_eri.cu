@@ -34,13 +34,16 @@ __device__ __forceinline__ int contract_g1(const EriLaunch& L, int bra, int ket,
       for (int m = 0; m <= ci.Lt; ++m) V[m * st] = Gm[m];
       for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
         const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = 0; o < n; ++o) vrr_bra(ld_op(kVrrOps, off + o), V, st, c);
+        for (int o = 0; o < n; ++o) vrr_bra<true>(ld_op(kVrrOps, off + o), V, S, st, c);
       }
       for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
         const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = 0; o < n; ++o) vrr_ket(ld_op(kVrrOps, off + o), V, st, c);
+        for (int o = 0; o < n; ++o) vrr_ket<true>(ld_op(kVrrOps, off + o), V, S, st, c);
       }
-      for (int a = 0; a < ci.n_acc; ++a) S[a * st] += V[__ldg(kAccSrc + ci.acc_off + a) * st];
+      for (int a = 0; a < ci.n_accl; ++a) {
+        const uint32_t w = __ldg(kAccSrc + ci.acc_off + a);
+        S[(w & 0xFFFF) * st] += V[(w >> 16) * st];
+      }
     }
   }
   if (!any) return 0;
@@ -92,15 +95,18 @@ __device__ __forceinline__ int contract_g32(const EriLaunch& L, int bra, int ket
       __syncwarp();
       for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
         const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = lane; o < n; o += 32) vrr_bra(ld_op(kVrrOps, off + o), V, 1, c);
+        for (int o = lane; o < n; o += 32) vrr_bra<false>(ld_op(kVrrOps, off + o), V, S, 1, c);
         __syncwarp();
       }
       for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
         const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = lane; o < n; o += 32) vrr_ket(ld_op(kVrrOps, off + o), V, 1, c);
+        for (int o = lane; o < n; o += 32) vrr_ket<false>(ld_op(kVrrOps, off + o), V, S, 1, c);
         __syncwarp();
       }
-      for (int a = lane; a < ci.n_acc; a += 32) S[a] += V[__ldg(kAccSrc + ci.acc_off + a)];
+      for (int a = lane; a < ci.n_accl; a += 32) {
+        const uint32_t w = __ldg(kAccSrc + ci.acc_off + a);
+        S[w & 0xFFFF] += V[w >> 16];
+      }
       __syncwarp();
     }
     __syncwarp();  // every lane is done with this chunk's coefficient sets
@@ -119,6 +125,23 @@ __device__ __forceinline__ int contract_g32(const EriLaunch& L, int bra, int ket
   return any;
 }
 
+#ifndef HFX_G1_MINB
+#define HFX_G1_MINB 6
+#endif
+#ifndef HFX_G32_MINB
+#define HFX_G32_MINB 6
+#endif
+
+// The digest reads P_bd, P_bc, P_ad, P_ac: if all four blocks are exactly zero the
+// quartet contributes exactly nothing.
+__device__ __forceinline__ bool zero_p_blocks(const EriLaunch& L, int sa, int sb, int sc, int sd) {
+  if (!L.pmax) return false;
+  const double* pm = L.pmax;
+  const size_t ns = L.ns;
+  return __ldg(pm + sb * ns + sd) == 0.0 && __ldg(pm + sb * ns + sc) == 0.0 &&
+         __ldg(pm + sa * ns + sd) == 0.0 && __ldg(pm + sa * ns + sc) == 0.0;
+}
+
 __device__ __forceinline__ void record_busy(const EriLaunch& L, unsigned long long t0) {
   if (L.busy && threadIdx.x == 0) {
     unsigned smid;
@@ -128,7 +151,7 @@ __device__ __forceinline__ void record_busy(const EriLaunch& L, unsigned long lo
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(64) eri_g1_kernel(const EriLaunch L) {
+__global__ void __launch_bounds__(64, HFX_G1_MINB) eri_g1_kernel(const EriLaunch L) {
   extern __shared__ double smem[];
   const int st = blockDim.x;
   double* S = smem + threadIdx.x;
@@ -137,23 +160,40 @@ __global__ void __launch_bounds__(64) eri_g1_kernel(const EriLaunch L) {
   unsigned long long t0 = 0, n_prim = 0, n_skip = 0, n_quart = 0;
   if (L.busy && threadIdx.x == 0) t0 = globaltimer_ns();
   if (MODE == 0) {
+    // a warp works on a range of the quartet list (an even share, or chunks claimed from
+    // the device counter); its lanes take interleaved quartets of the range, so
+    // neighbouring lanes work on neighbouring quartets
+    const int lane = threadIdx.x & 31;
     long long q0, q1;
-    group_range(L, gid, ng, q0, q1);
-    if (q0 < q1) {
-      int r = find_row(L.qoff, L.row_begin, L.row_end, q0);
-      for (long long q = q0; q < q1; ++q) {
+    bool more = true;
+    if (L.schedule != 2) group_range(L, gid >> 5, ng >> 5, q0, q1);
+    while (more) {
+      if (L.schedule == 2) {
+        unsigned long long c0 = 0;
+        if (lane == 0) c0 = atomicAdd(L.work, (unsigned long long)L.chunk);
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if ((long long)c0 >= L.q_count) break;
+        q0 = L.q_begin + (long long)c0;
+        q1 = min(q0 + L.chunk, L.q_begin + L.q_count);
+      } else {
+        more = false;
+      }
+      if (q0 + lane >= q1) continue;
+      int r = find_row(L.qoff, L.row_begin, L.row_end, q0 + lane);
+      for (long long q = q0 + lane; q < q1; q += 32) {
         while (__ldg(L.qoff + r + 1) <= q) ++r;
         const int bra_s = L.bra_bin_start + (r - L.row_begin);
         const int ket_s = L.ket_bin_start + (int)(q - __ldg(L.qoff + r));
         const int bra = __ldg(L.sorted + bra_s), ket = __ldg(L.sorted + ket_s);
+        const int sa = __ldg(L.pa.sa + bra), sb = __ldg(L.pa.sb + bra);
+        const int sc = __ldg(L.pa.sa + ket), sd = __ldg(L.pa.sb + ket);
+        if (zero_p_blocks(L, sa, sb, sc, sd)) continue;
         const int npq = __ldg(L.pa.prim_n + bra) * __ldg(L.pa.prim_n + ket);
         const int ne = contract_g1(L, bra, ket, S, st);
         n_prim += ne;
         n_skip += npq - ne;
         if (!ne) continue;
         ++n_quart;
-        const int sa = __ldg(L.pa.sa + bra), sb = __ldg(L.pa.sb + bra);
-        const int sc = __ldg(L.pa.sa + ket), sd = __ldg(L.pa.sb + ket);
         double deg = 1.0;
         if (sa == sb) deg *= 0.5;
         if (sc == sd) deg *= 0.5;
@@ -179,7 +219,7 @@ __global__ void __launch_bounds__(64) eri_g1_kernel(const EriLaunch L) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(64) eri_g32_kernel(const EriLaunch L, int group_stride) {
+__global__ void __launch_bounds__(64, HFX_G32_MINB) eri_g32_kernel(const EriLaunch L, int group_stride) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gpb = blockDim.x >> 5;
@@ -191,22 +231,35 @@ __global__ void __launch_bounds__(64) eri_g32_kernel(const EriLaunch L, int grou
   if (L.busy && threadIdx.x == 0) t0 = globaltimer_ns();
   if (MODE == 0) {
     long long q0, q1;
-    group_range(L, gid, ng, q0, q1);
-    if (q0 < q1) {
+    bool more = true;
+    if (L.schedule != 2) group_range(L, gid, ng, q0, q1);
+    while (more) {
+      if (L.schedule == 2) {
+        unsigned long long c0 = 0;
+        if (lane == 0) c0 = atomicAdd(L.work, (unsigned long long)L.chunk);
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if ((long long)c0 >= L.q_count) break;
+        q0 = L.q_begin + (long long)c0;
+        q1 = min(q0 + L.chunk, L.q_begin + L.q_count);
+      } else {
+        more = false;
+      }
+      if (q0 >= q1) continue;
       int r = find_row(L.qoff, L.row_begin, L.row_end, q0);
       for (long long q = q0; q < q1; ++q) {
         while (__ldg(L.qoff + r + 1) <= q) ++r;
         const int bra_s = L.bra_bin_start + (r - L.row_begin);
         const int ket_s = L.ket_bin_start + (int)(q - __ldg(L.qoff + r));
         const int bra = __ldg(L.sorted + bra_s), ket = __ldg(L.sorted + ket_s);
+        const int sa = __ldg(L.pa.sa + bra), sb = __ldg(L.pa.sb + bra);
+        const int sc = __ldg(L.pa.sa + ket), sd = __ldg(L.pa.sb + ket);
+        if (zero_p_blocks(L, sa, sb, sc, sd)) continue;
         const int npq = __ldg(L.pa.prim_n + bra) * __ldg(L.pa.prim_n + ket);
         const int ne = contract_g32(L, bra, ket, S, CF, lane);
         n_prim += ne;
         n_skip += npq - ne;
         if (!ne) continue;
         ++n_quart;
-        const int sa = __ldg(L.pa.sa + bra), sb = __ldg(L.pa.sb + bra);
-        const int sc = __ldg(L.pa.sa + ket), sd = __ldg(L.pa.sb + ket);
         double deg = 1.0;
         if (sa == sb) deg *= 0.5;
         if (sc == sd) deg *= 0.5;
@@ -240,7 +293,7 @@ static const int kBlock = 64;
 
 int eri_group_size(int cls) {
   // thread-per-quartet for classes whose scratch fits comfortably; warp otherwise
-  return kClassInfo[cls].scratch <= 100 ? 1 : 32;
+  return kClassInfo[cls].scratch <= HFX_G1_MAX_SCRATCH ? 1 : 32;
 }
 
 static int g32_stride(int cls) {

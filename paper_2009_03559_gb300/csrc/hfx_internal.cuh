@@ -13,7 +13,9 @@ struct EriClassInfo {
   int n_acc, work_base, scratch;       // group scratch (doubles): acc | VRR slots
   int n_bra_lv, n_ket_lv;
   int lv_off[8], lv_n[8];              // VRR levels: op offset (in uint4) and count
-  int acc_off;                         // into kAccSrc
+  int acc_off;                         // into kAccSrc: (acc index | slot << 16) entries
+  int n_accl;                          // accumulators added after the levels (others are
+                                       // accumulated by the op that makes them)
   int n_post;                          // post-contraction stages
   int post_type[8], post_off[8], post_n[8];  // 0 bra HRR, 1 ket HRR, 2 spherical
   int out_base;                        // final spherical block in group scratch
@@ -151,7 +153,9 @@ struct EriLaunch {
   int row_begin, row_end;     // rows of this class pair
   int bra_bin_start, ket_bin_start;
   long long q_begin, q_count; // quartet range of this class pair
-  int schedule;               // 0 quartet split, 1 bra-pair split
+  int schedule;               // 0 quartet split, 1 bra-pair split, 2 dynamic chunks
+  unsigned long long* work;   // schedule 2: next unclaimed quartet (relative to q_begin)
+  int chunk;                  // schedule 2: quartets per claim
   const double* boys;
   double omega2;
   const double* P;
@@ -163,6 +167,9 @@ struct EriLaunch {
   double* diag_Q;
   unsigned long long* busy;     // optional per-SM globaltimer busy ns (indexed by %smid)
   unsigned long long* counters; // optional: [0] primitive quartets evaluated, [1] quartets, [2] skipped
+  const double* pmax;           // optional: max |P| of each shell-pair block (ns x ns); quartets
+  int ns;                       // whose four density blocks are all zero are skipped
 };
+
 
 }  // namespace hfx

@@ -199,6 +199,19 @@ __global__ void k_gather_bounds(RowTable rt, const long long* __restrict__ qoff,
   if (i < 22) out[i] = qoff[rt.row_base[i]];
 }
 
+// max |P| over each shell-pair block (I, J): one thread per block
+__global__ void k_pmax(int ns, const int* __restrict__ bf_off, const int* __restrict__ l,
+                       const double* __restrict__ P, int ld, double* __restrict__ pmax) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ns * ns) return;
+  const int I = (int)(t / ns), J = (int)(t - (long long)I * ns);
+  const int oi = bf_off[I], oj = bf_off[J], ni = 2 * l[I] + 1, nj = 2 * l[J] + 1;
+  double m = 0.0;
+  for (int a = 0; a < ni; ++a)
+    for (int b = 0; b < nj; ++b) m = fmax(m, fabs(P[(size_t)(oi + a) * ld + oj + b]));
+  pmax[t] = m;
+}
+
 // ---------------------------------------------------------------------------
 // K = A + A^T in place, 32x32 tiles (tile pairs bi <= bj), then E = sum P K with
 // compensated (Neumaier) summation.
@@ -418,6 +431,14 @@ cudaError_t launch_finalize(int n, int ld, const double* P, double* K, double* p
   k_symmetrize<<<(unsigned)(nt * (nt + 1) / 2), dim3(32, 8), 0, s>>>(n, ld, K);
   k_trace_partial<<<n_part, 256, 0, s>>>(n, ld, P, K, part);
   k_trace_final<<<1, 256, 0, s>>>(n_part, part, energy);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pmax(int ns, const int* bf_off, const int* l, const double* P, int ld, double* pmax,
+                        cudaStream_t s) {
+  const long long n = (long long)ns * ns;
+  if (n <= 0) return cudaSuccess;
+  k_pmax<<<nblk(n, 256), 256, 0, s>>>(ns, bf_off, l, P, ld, pmax);
   return cudaGetLastError();
 }
 

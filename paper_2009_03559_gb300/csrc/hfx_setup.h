@@ -44,6 +44,8 @@ cudaError_t launch_count(int n_rows, const RowTable& rt, const double* Qs, doubl
 cudaError_t launch_gather_bounds(const RowTable& rt, const long long* qoff, long long* out, cudaStream_t s);
 cudaError_t launch_finalize(int n, int ld, const double* P, double* K, double* part, int n_part, double* energy,
                             cudaStream_t s);
+cudaError_t launch_pmax(int ns, const int* bf_off, const int* l, const double* P, int ld, double* pmax,
+                        cudaStream_t s);
 cudaError_t fma_peak(double* fp64_tflops, double* fp32_tflops);
 
 }  // namespace hfx

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libhfx.so")
 
 HFX_FP64, HFX_MIXED = 0, 1
-HFX_SCHED_QUARTET, HFX_SCHED_PAIR = 0, 1
+HFX_SCHED_QUARTET, HFX_SCHED_PAIR, HFX_SCHED_DYNAMIC = 0, 1, 2
 ERR_NAMES = {0: "OK", -1: "ARG", -2: "UNSUPPORTED_L", -3: "OOM", -4: "CUDA", -5: "STATE", -6: "TIMEOUT"}
 
 PAIR_CLASSES = ["ss", "ps", "pp", "ds", "dp", "dd"]
@@ -25,13 +25,14 @@ QUARTET_CLASSES = [f"({PAIR_CLASSES[hi]}|{PAIR_CLASSES[lo]})" for hi in range(6)
 class Options(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("schwarz_tau", ctypes.c_double), ("rcut_bohr", ctypes.c_double),
                 ("prim_tau", ctypes.c_double), ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("skip_zero_p", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("n_pairs_cutoff", ctypes.c_int64), ("n_pairs_kept", ctypes.c_int64),
                 ("n_quartets", ctypes.c_int64), ("n_quartets_class", ctypes.c_int64 * 21),
                 ("prim_quartets_class", ctypes.c_int64 * 21),
+                ("quartets_evaluated_class", ctypes.c_int64 * 21),
                 ("flops_fp64", ctypes.c_double), ("flops_class", ctypes.c_double * 21),
                 ("group_size_class", ctypes.c_int32 * 21),
                 ("ms_pairs", ctypes.c_double), ("ms_build", ctypes.c_double),
@@ -42,6 +43,7 @@ class Stats(ctypes.Structure):
             "n_pairs_cutoff": int(self.n_pairs_cutoff), "n_pairs_kept": int(self.n_pairs_kept),
             "n_quartets": int(self.n_quartets), "n_quartets_class": [int(x) for x in self.n_quartets_class],
             "prim_quartets_class": [int(x) for x in self.prim_quartets_class],
+            "quartets_evaluated_class": [int(x) for x in self.quartets_evaluated_class],
             "flops_fp64": float(self.flops_fp64), "flops_class": [float(x) for x in self.flops_class],
             "group_size_class": [int(x) for x in self.group_size_class], "ms_pairs": float(self.ms_pairs),
             "ms_build": float(self.ms_build), "ms_class": [float(x) for x in self.ms_class],
@@ -135,8 +137,8 @@ class HFX:
     current stream).  ``build_K(P)`` takes and returns torch CUDA float64 tensors.
     """
 
-    def __init__(self, system, stream=None, tau=None, rcut=None, omega=None, schedule=HFX_SCHED_QUARTET,
-                 prim_tau=None):
+    def __init__(self, system, stream=None, tau=None, rcut=None, omega=None, schedule=HFX_SCHED_DYNAMIC,
+                 prim_tau=None, skip_zero_p=True):
         import torch  # device memory and streams only
         if not torch.cuda.is_available():
             raise RuntimeError("HFX needs a CUDA device; there is no CPU path")
@@ -151,6 +153,7 @@ class HFX:
         if prim_tau is not None:
             o.prim_tau = prim_tau
         o.schedule = schedule
+        o.skip_zero_p = 1 if skip_zero_p else 0
         self.options = o
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         xyz, sa, sl, sn, al, co = system.basis_arrays()

@@ -123,13 +123,17 @@ def test_coulomb_limit(hfx_mod):
     assert abs(e - eo) <= TOL_E * max(1.0, abs(eo))
 
 
-def test_pair_schedule_same_K(hfx_mod):
-    """The parallel-pair split (Algorithm 2) and the quartet split give the same K."""
+@pytest.mark.parametrize("skip", [True, False])
+def test_schedules_same_K(hfx_mod, skip):
+    """The static parallel-pair split (Algorithm 2), the static quartet split (Algorithm 3)
+    and the dynamic chunk distribution give the same K, with and without the skip of
+    quartets whose density blocks are exactly zero."""
     s, P = inputs.config1(8)
-    h1, K1, e1 = gpu_build(hfx_mod, s, P, schedule=hfx_mod.HFX_SCHED_QUARTET)
-    h2, K2, e2 = gpu_build(hfx_mod, s, P, schedule=hfx_mod.HFX_SCHED_PAIR)
-    assert np.abs(K1 - K2).max() <= 1e-12
-    assert abs(e1 - e2) <= 1e-12
+    out = [gpu_build(hfx_mod, s, P, schedule=sch, skip_zero_p=skip)
+           for sch in (hfx_mod.HFX_SCHED_QUARTET, hfx_mod.HFX_SCHED_PAIR, hfx_mod.HFX_SCHED_DYNAMIC)]
+    for h, K, e in out[1:]:
+        assert np.abs(K - out[0][1]).max() <= 1e-12
+        assert abs(e - out[0][2]) <= 1e-12
 
 
 def test_host_entry_point(hfx_mod):
