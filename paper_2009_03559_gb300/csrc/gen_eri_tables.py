@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import json
 import math
+import os
 import sys
 
 PAIR_CLASSES = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
@@ -34,7 +35,7 @@ FOLD = "--no-fold" not in sys.argv
 # classes whose group scratch fits in this many doubles run one quartet per thread
 # (the kernels read this limit from the generated header); only those fold their
 # accumulation into the VRR ops, which measured faster there and slower for warp groups
-G1_MAX_SCRATCH = 100
+G1_MAX_SCRATCH = int(os.environ.get("HFX_G1_MAX_SCRATCH", "100"))
 
 
 def monos(l):
