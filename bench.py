@@ -31,10 +31,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "HFX K-build ms & screened ERI quartets/s vs plain FP64; p50/p99 latency"
-def workload_desc(s):
+def workload_desc(s, mixed=False, fp32_classes="all"):
+    prec = ("mixed precision (FP32 recurrences where Q*Q*max|P| < 1e-6, "
+            f"{'all classes' if fp32_classes == 'all' else 's,p classes only'}; FP64 Boys and K)"
+            if mixed else "plain FP64")
     return (f"diamond-{s.n_atoms} DZP-like: {s.n_atoms} atoms (a=10.26 bohr cells), {s.n_shells} shells "
             f"s,s,p,p,d, {s.n_bf} spherical functions, 3 primitives/shell, omega=0.11, r_c=6 bohr, "
-            f"tau=1e-8, P truncated beyond 10 bohr; plain FP64")
+            f"tau=1e-8, P truncated beyond 10 bohr; {prec}")
 
 
 WORKLOAD = ("diamond-64 DZP-like: 64 atoms (2x2x2 cells, a=10.26 bohr), 320 shells s,s,p,p,d, "
@@ -177,6 +180,9 @@ def main():
                     help="diamond piece size (64 = the benchmark workload; smaller for profiler captures)")
     ap.add_argument("--report", action="store_true", help="per-class table on stderr")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--fp32-classes", default="sp", choices=["all", "sp"])
+    ap.add_argument("--fp32-tau", type=float, default=1e-6)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_info()
@@ -198,7 +204,10 @@ def main():
 
     s, P_np = inputs.config1(args.atoms)
     stream = torch.cuda.Stream()
-    h = hfx.HFX(s, stream=stream)
+    mixed = args.precision == "mixed"
+    h = hfx.HFX(s, stream=stream, precision=hfx.HFX_MIXED if mixed else hfx.HFX_FP64,
+                fp32_class_mask=((1 << 21) - 1) if args.fp32_classes == "all" else hfx.SP_CLASS_MASK,
+                fp32_tau=args.fp32_tau)
     h.build_pairs()
     P = torch.from_numpy(P_np).cuda()
     K = torch.empty_like(P)
@@ -250,7 +259,7 @@ def main():
     # roofline of the dominant kernel: the warp-cooperative FP64 kernel (classes with G=32)
     from paper_2009_03559_gb300.hfx import QUARTET_CLASSES
     ms_cls = st_timed["ms_class"]
-    g32 = [c for c in range(21) if st_timed["group_size_class"][c] == 32]
+    g32 = [c for c in range(21) if st_timed["group_size_class"][c] == 32 or mixed]
     flops_cls = st_timed["flops_class"]
     dom_ms = sum(ms_cls[c] for c in g32)
     dom_fl = sum(flops_cls[c] for c in g32)
@@ -265,9 +274,10 @@ def main():
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps,
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if not mixed else "f64+f32",
             "data": "synthetic",
-            "config": {"workload": workload_desc(s), "n_bf": s.n_bf, "quartets_per_step": n_q,
+            "config": {"workload": workload_desc(s, mixed, args.fp32_classes), "n_bf": s.n_bf, "quartets_per_step": n_q,
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{ws}",
                        "energy_E_K": energy},
             "e2e": {"value": n_q / float(np.median(e2e_t)) if e2e_t else None, "unit": "quartets/s",
@@ -279,6 +289,9 @@ def main():
                          "peak_source": "FP64 FMA-chain probe of this run (hfx_measure_fma_peak)"},
             "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"]},
             "fp64_flops_per_step": st_timed["flops_fp64"],
+            "fp32_flops_per_step": st_timed["flops_fp32"],
+            "quartets_evaluated_per_step": sum(st_timed["quartets_evaluated_class"]),
+            "quartets_fp32_per_step": sum(st_timed["quartets_fp32_class"]),
             "fp64_tflops_step": st_timed["flops_fp64"] / (total_ms / args.steps * 1e-3) / 1e12,
             "fp32_peak_tflops": fp32_peak,
             "class_ms": {QUARTET_CLASSES[c]: round(ms_cls[c], 3) for c in range(21)},

@@ -53,7 +53,7 @@ extern "C" {
 
 /* precision modes */
 #define HFX_FP64 0                /* every integral in FP64 */
-#define HFX_MIXED 1               /* small-bound s,p quartets in FP32, see hfx_options */
+#define HFX_MIXED 1               /* FP32 recurrences for small-bound quartets, see hfx_options */
 
 /* work schedules inside a class launch (paper Sec. 3.2, Algorithms 2 and 3) */
 #define HFX_SCHED_QUARTET 0       /* static even split of the screened quartet list */
@@ -68,11 +68,17 @@ typedef struct {
   double schwarz_tau;  /* Schwarz threshold tau (>= 0) */
   double rcut_bohr;    /* orbital cutoff radius r_c; <= 0 disables the pair-distance screen */
   double prim_tau;     /* primitive pairs with |prefactor| below this are dropped (default 1e-22) */
-  int precision;       /* HFX_FP64 (only mode of this version) */
+  double fp32_tau;     /* HFX_MIXED: a quartet's recurrences (VRR, HRR, spherical step) run in FP32
+                          iff Q_IJ Q_KL max(|P_bd|,|P_bc|,|P_ad|,|P_ac|) < fp32_tau (default 1e-6);
+                          the Boys step and all K accumulation stay FP64 */
+  int precision;       /* HFX_FP64 (default) or HFX_MIXED */
   int schedule;        /* HFX_SCHED_DYNAMIC (default), HFX_SCHED_QUARTET or HFX_SCHED_PAIR */
   int skip_zero_p;     /* 1 (default): skip quartets whose four density blocks P_bd, P_bc,
                           P_ad, P_ac are all exactly zero (their contribution is exactly 0) */
-  int reserved[5];     /* set to 0 */
+  int fp32_class_mask; /* HFX_MIXED: bit c allows FP32 for quartet class c (index as in
+                          n_quartets_class); default 0x3F = the six classes without d shells
+                          (recurrences of d classes stay FP64) */
+  int reserved[4];     /* set to 0 */
 } hfx_options;
 
 typedef struct {
@@ -84,6 +90,8 @@ typedef struct {
   int64_t prim_quartets_class[21]; /* primitive quartets evaluated per class (timed builds) */
   int64_t quartets_evaluated_class[21]; /* quartets evaluated per class (timed builds): the kept
                                   quartets minus those skipped for exactly-zero density blocks */
+  int64_t quartets_fp32_class[21]; /* of those, evaluated with FP32 recurrences (HFX_MIXED) */
+  double flops_fp32;           /* FP32 flops of the last timed build (same model) */
   double flops_fp64;           /* FP64 flops of the last timed K build (operation-count model
                                   of the kernels: add/mul = 1, fma = 2) */
   double flops_class[21];      /* the same per class */

@@ -23,6 +23,19 @@ namespace hfx {
 
 __device__ __constant__ double kSphCoef[6] = {0.0, 1.0, -0.28867513459481287, 0.57735026918962573,
                                               0.5, -0.5};
+__device__ __constant__ float kSphCoefF[6] = {0.0f, 1.0f, -0.28867513459481287f, 0.57735026918962573f,
+                                              0.5f, -0.5f};
+
+// fused multiply-add in the precision of the arguments (an unqualified fma() on floats
+// would promote to FP64, which runs on the FP64 pipe together with the conversions)
+__device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename R>
+__device__ __forceinline__ R sph_coef(int i);
+template <>
+__device__ __forceinline__ float sph_coef<float>(int i) { return kSphCoefF[i]; }
+template <>
+__device__ __forceinline__ double sph_coef<double>(int i) { return kSphCoef[i]; }
 
 // coefficient set of one primitive quartet (shared-memory layout for G > 1)
 enum {
@@ -54,18 +67,20 @@ struct CoefRg {
   __device__ __forceinline__ double rq() const { return RQ; }
 };
 
-// Coefficients read from shared memory (G > 1).
+// Coefficients read from shared memory (G > 1), stored in the precision R of the
+// recurrences (FP64, or FP32 for quartets selected for FP32).
+template <typename R>
 struct CoefSm {
-  const double* c;
-  __device__ __forceinline__ double pa(int i) const { return c[CF_PA + i]; }
-  __device__ __forceinline__ double wp(int i) const { return c[CF_WP + i]; }
-  __device__ __forceinline__ double qc(int i) const { return c[CF_QC + i]; }
-  __device__ __forceinline__ double wq(int i) const { return c[CF_WQ + i]; }
-  __device__ __forceinline__ double ca(int n) const { return c[CF_CA + n]; }
-  __device__ __forceinline__ double ck(int n) const { return c[CF_CK + n]; }
-  __device__ __forceinline__ double cb(int n) const { return c[CF_CB + n]; }
-  __device__ __forceinline__ double rp() const { return c[CF_RP]; }
-  __device__ __forceinline__ double rq() const { return c[CF_RQ]; }
+  const R* c;
+  __device__ __forceinline__ R pa(int i) const { return c[CF_PA + i]; }
+  __device__ __forceinline__ R wp(int i) const { return c[CF_WP + i]; }
+  __device__ __forceinline__ R qc(int i) const { return c[CF_QC + i]; }
+  __device__ __forceinline__ R wq(int i) const { return c[CF_WQ + i]; }
+  __device__ __forceinline__ R ca(int n) const { return c[CF_CA + n]; }
+  __device__ __forceinline__ R ck(int n) const { return c[CF_CK + n]; }
+  __device__ __forceinline__ R cb(int n) const { return c[CF_CB + n]; }
+  __device__ __forceinline__ R rp() const { return c[CF_RP]; }
+  __device__ __forceinline__ R rq() const { return c[CF_RQ]; }
 };
 
 // Primitive-quartet set-up.  Fills the register coefficient set and returns the
@@ -122,8 +137,61 @@ __device__ __forceinline__ bool prim_setup(const PrimPair& b, const PrimPair& k,
   return true;
 }
 
-__device__ __forceinline__ void store_coef(const CoefRg& c, const double* Gm, int Lt, bool ok, double* cf) {
-  cf[CF_SKIP] = ok ? 0.0 : 1.0;
+// Set-up for the FP32 recurrences: the Boys step (rho, kappa, T, G_m, the prefactor) in FP64
+// exactly as in prim_setup, the VRR coefficients in FP32 from the float copies of the pair
+// data; only the G_m values are converted.  Writes the coefficient set cf (floats).
+__device__ __forceinline__ void prim_setup_f32(const PrimPair& b, const PrimPair& k, int E, int F, int Lt,
+                                               double omega2, const double* __restrict__ tab, float* cf) {
+  const double p = b.p, q = k.p;
+  const double s = p + q;
+  const double inv_s = rcp_nr(s);
+  const double rho = p * (q * inv_s);
+  const double PQ0 = b.P[0] - k.P[0], PQ1 = b.P[1] - k.P[1], PQ2 = b.P[2] - k.P[2];
+  const double T = rho * fma(PQ0, PQ0, fma(PQ1, PQ1, PQ2 * PQ2));
+  double F1[kMaxLt + 1], F2[kMaxLt + 1];
+  const double pref = b.C * k.C * rsqrt_nr(s);
+  if (omega2 > 0.0) {
+    const double kap = omega2 * rcp_nr(omega2 + rho);
+    const double kT = kap * T;
+    if (kT >= kBoysXmax) {
+      cf[CF_SKIP] = 1.f;
+      return;
+    }
+    boys_eval(Lt, T, tab, F1);
+    boys_eval(Lt, kT, tab, F2);
+    double a = pref * (kap * rsqrt_nr(kap));
+    for (int m = 0; m <= Lt; ++m) {
+      cf[CF_G + m] = (float)fma(-a, F2[m], pref * F1[m]);
+      a *= kap;
+    }
+  } else {
+    boys_eval(Lt, T, tab, F1);
+    for (int m = 0; m <= Lt; ++m) cf[CF_G + m] = (float)(pref * F1[m]);
+  }
+  cf[CF_SKIP] = 0.f;
+  const float pf = b.pf, qf = k.pf;
+  const float inv_sf = __frcp_rn(pf + qf);
+  const float RP = qf * inv_sf, RQ = pf * inv_sf;
+  const float d0 = (float)PQ0, d1 = (float)PQ1, d2 = (float)PQ2;
+  if (E > 0) {
+    cf[CF_PA + 0] = b.PAf[0]; cf[CF_PA + 1] = b.PAf[1]; cf[CF_PA + 2] = b.PAf[2];
+    cf[CF_WP + 0] = -RP * d0; cf[CF_WP + 1] = -RP * d1; cf[CF_WP + 2] = -RP * d2;
+    cf[CF_CA + 1] = b.inv2pf; cf[CF_CA + 2] = 2.f * b.inv2pf; cf[CF_CA + 3] = 3.f * b.inv2pf;
+    cf[CF_RP] = RP;
+  }
+  if (F > 0) {
+    cf[CF_QC + 0] = k.PAf[0]; cf[CF_QC + 1] = k.PAf[1]; cf[CF_QC + 2] = k.PAf[2];
+    cf[CF_WQ + 0] = RQ * d0; cf[CF_WQ + 1] = RQ * d1; cf[CF_WQ + 2] = RQ * d2;
+    cf[CF_CK + 1] = k.inv2pf; cf[CF_CK + 2] = 2.f * k.inv2pf; cf[CF_CK + 3] = 3.f * k.inv2pf;
+    cf[CF_RQ] = RQ;
+    const float h = 0.5f * inv_sf;
+    cf[CF_CB + 1] = h; cf[CF_CB + 2] = 2.f * h; cf[CF_CB + 3] = 3.f * h; cf[CF_CB + 4] = 4.f * h;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_coef(const CoefRg& c, const double* Gm, int Lt, bool ok, R* cf) {
+  cf[CF_SKIP] = ok ? R(0) : R(1);
   if (!ok) return;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -150,30 +218,30 @@ __device__ __forceinline__ uint4 ld_op(const uint32_t* base, int idx) {
 // The result is stored to V[dst]; ops flagged "acc" (targets no op reads) instead add it
 // to the accumulator S[dst], starting their FMA chain from the accumulator value.
 // FOLD = false compiles the plain form (no accumulator branch) for classes without folding.
-template <bool FOLD, class Coef>
-__device__ __forceinline__ void vrr_bra(uint4 op, double* V, double* S, int st, const Coef& c) {
+template <bool FOLD, typename R, class Coef>
+__device__ __forceinline__ void vrr_bra(uint4 op, R* V, R* S, int st, const Coef& c) {
   const int dst = op.x & 0xFFFF, s1 = op.x >> 16, s2 = op.y & 0xFFFF, s3 = op.y >> 16, s4 = op.z & 0xFFFF;
   const int i = op.w & 3, nA = (op.w >> 2) & 7;
   const bool acc = FOLD && ((op.w >> 8) & 1);
-  double v = acc ? fma(c.pa(i), V[s1 * st], S[dst * st]) : c.pa(i) * V[s1 * st];
-  v = fma(c.wp(i), V[s2 * st], v);
-  if (nA) v = fma(c.ca(nA), fma(-c.rp(), V[s4 * st], V[s3 * st]), v);
+  R v = acc ? fmar(c.pa(i), V[s1 * st], S[dst * st]) : c.pa(i) * V[s1 * st];
+  v = fmar(c.wp(i), V[s2 * st], v);
+  if (nA) v = fmar(c.ca(nA), fmar(-c.rp(), V[s4 * st], V[s3 * st]), v);
   if (acc)
     S[dst * st] = v;
   else
     V[dst * st] = v;
 }
 
-template <bool FOLD, class Coef>
-__device__ __forceinline__ void vrr_ket(uint4 op, double* V, double* S, int st, const Coef& c) {
+template <bool FOLD, typename R, class Coef>
+__device__ __forceinline__ void vrr_ket(uint4 op, R* V, R* S, int st, const Coef& c) {
   const int dst = op.x & 0xFFFF, s1 = op.x >> 16, s2 = op.y & 0xFFFF, s3 = op.y >> 16;
   const int s4 = op.z & 0xFFFF, s5 = op.z >> 16;
   const int i = op.w & 3, nA = (op.w >> 2) & 7, nB = (op.w >> 5) & 7;
   const bool acc = FOLD && ((op.w >> 8) & 1);
-  double v = acc ? fma(c.qc(i), V[s1 * st], S[dst * st]) : c.qc(i) * V[s1 * st];
-  v = fma(c.wq(i), V[s2 * st], v);
-  if (nA) v = fma(c.ck(nA), fma(-c.rq(), V[s4 * st], V[s3 * st]), v);
-  if (nB) v = fma(c.cb(nB), V[s5 * st], v);
+  R v = acc ? fmar(c.qc(i), V[s1 * st], S[dst * st]) : c.qc(i) * V[s1 * st];
+  v = fmar(c.wq(i), V[s2 * st], v);
+  if (nA) v = fmar(c.ck(nA), fmar(-c.rq(), V[s4 * st], V[s3 * st]), v);
+  if (nB) v = fmar(c.cb(nB), V[s5 * st], v);
   if (acc)
     S[dst * st] = v;
   else
@@ -181,26 +249,27 @@ __device__ __forceinline__ void vrr_ket(uint4 op, double* V, double* S, int st, 
 }
 
 // Post-contraction op on the group scratch S.
-__device__ __forceinline__ void post_op(uint4 op, int type, double* S, int st, const double* AB,
-                                        const double* CD) {
+template <typename R>
+__device__ __forceinline__ void post_op(uint4 op, int type, R* S, int st, const R* AB, const R* CD) {
   const int dst = op.x & 0xFFFF, s1 = op.x >> 16, s2 = op.y & 0xFFFF, s3 = op.y >> 16;
-  double v;
+  R v;
   if (type == 2) {
     const int c0 = op.z & 15, c1 = (op.z >> 4) & 15, c2 = (op.z >> 8) & 15;
-    v = kSphCoef[c0] * S[s1 * st];
-    if (c1) v = fma(kSphCoef[c1], S[s2 * st], v);
-    if (c2) v = fma(kSphCoef[c2], S[s3 * st], v);
+    v = sph_coef<R>(c0) * S[s1 * st];
+    if (c1) v = fmar(sph_coef<R>(c1), S[s2 * st], v);
+    if (c2) v = fmar(sph_coef<R>(c2), S[s3 * st], v);
   } else {
     const int i = (op.z >> 12) & 3;
-    const double d = (type == 0) ? AB[i] : CD[i];
-    v = fma(d, S[s2 * st], S[s1 * st]);
+    const R d = (type == 0) ? AB[i] : CD[i];
+    v = fmar(d, S[s2 * st], S[s1 * st]);
   }
   S[dst * st] = v;
 }
 
 // Digest of the final spherical block v (stride st) into the half matrix A.
 // Outputs o in [o0, nout) step ostep (lanes of the group).
-__device__ __forceinline__ void digest(const EriClassInfo& ci, const double* v, int st, int A, int B,
+template <typename R>
+__device__ __forceinline__ void digest(const EriClassInfo& ci, const R* v, int st, int A, int B,
                                        int C, int D, double deg, const double* __restrict__ P,
                                        double* K, int ld, int o0, int ostep) {
   const int na = ci.dims[0], nb = ci.dims[1], nc = ci.dims[2], nd = ci.dims[3];
@@ -213,25 +282,25 @@ __device__ __forceinline__ void digest(const EriClassInfo& ci, const double* v, 
       const int a = o / nc, c = o - a * nc;
       for (int b = 0; b < nb; ++b)
         for (int d = 0; d < nd; ++d)
-          acc = fma(v[(((a * nb + b) * nc + c) * nd + d) * st], __ldg(P + (size_t)(B + b) * ld + D + d), acc);
+          acc = fma((double)v[(((a * nb + b) * nc + c) * nd + d) * st], __ldg(P + (size_t)(B + b) * ld + D + d), acc);
       row = A + a; col = C + c;
     } else if (o < nAC + nAD) {
       const int t = o - nAC, a = t / nd, d = t - a * nd;
       for (int b = 0; b < nb; ++b)
         for (int c = 0; c < nc; ++c)
-          acc = fma(v[(((a * nb + b) * nc + c) * nd + d) * st], __ldg(P + (size_t)(B + b) * ld + C + c), acc);
+          acc = fma((double)v[(((a * nb + b) * nc + c) * nd + d) * st], __ldg(P + (size_t)(B + b) * ld + C + c), acc);
       row = A + a; col = D + d;
     } else if (o < nAC + nAD + nBC) {
       const int t = o - nAC - nAD, b = t / nc, c = t - b * nc;
       for (int a = 0; a < na; ++a)
         for (int d = 0; d < nd; ++d)
-          acc = fma(v[(((a * nb + b) * nc + c) * nd + d) * st], __ldg(P + (size_t)(A + a) * ld + D + d), acc);
+          acc = fma((double)v[(((a * nb + b) * nc + c) * nd + d) * st], __ldg(P + (size_t)(A + a) * ld + D + d), acc);
       row = B + b; col = C + c;
     } else {
       const int t = o - nAC - nAD - nBC, b = t / nd, d = t - b * nd;
       for (int a = 0; a < na; ++a)
         for (int c = 0; c < nc; ++c)
-          acc = fma(v[(((a * nb + b) * nc + c) * nd + d) * st], __ldg(P + (size_t)(A + a) * ld + C + c), acc);
+          acc = fma((double)v[(((a * nb + b) * nc + c) * nd + d) * st], __ldg(P + (size_t)(A + a) * ld + C + c), acc);
       row = B + b; col = D + d;
     }
     atomicAdd(K + (size_t)row * ld + col, deg * acc);

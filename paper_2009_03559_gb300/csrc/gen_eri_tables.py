@@ -516,7 +516,7 @@ def emit(classes, f=sys.stdout):
             lst(r["lv_off"], 8), lst(r["lv_n"], 8), str(r["acc_off"]), str(len(c.acc_src)),
             str(len(c.stages)), lst(r["p_type"], 8), lst(r["p_off"], 8), lst(r["p_n"], 8),
             str(r["out_base"]), lst(c.final_dims, 4),
-            str(fl["vrr"] + fl["acc"]), str(fl["hrr"] + fl["sph"] + fl["digest"]),
+            str(fl["vrr"] + fl["acc"]), str(fl["hrr"] + fl["sph"] + fl["digest"]), str(fl["digest"]),
         ]) + "},\n")
     w("};\n")
 

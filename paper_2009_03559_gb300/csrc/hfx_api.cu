@@ -13,6 +13,10 @@
 
 using namespace hfx;
 
+// device counters per class: primitive quartets evaluated, quartets evaluated, primitive
+// quartets dropped at the Boys step, quartets in FP32, primitive quartets in FP32
+static const int kNCnt = 5;
+
 struct hfx_ctx {
   cudaStream_t stream = nullptr;
   hfx_options opt{};
@@ -38,7 +42,7 @@ struct hfx_ctx {
   int n_part = 0;
   double *d_Pst = nullptr, *d_Kst = nullptr;
   unsigned long long* d_busy = nullptr;      // per SM
-  unsigned long long* d_counters = nullptr;  // 3 per class
+  unsigned long long* d_counters = nullptr;  // kNCnt per class
   unsigned long long* d_work = nullptr;      // dynamic-schedule claim counter per class
   bool timing = false;
   cudaEvent_t ev[2 * 21 + 4] = {};
@@ -101,6 +105,10 @@ extern "C" void hfx_default_options(hfx_options* opt) {
   opt->precision = HFX_FP64;
   opt->schedule = HFX_SCHED_DYNAMIC;
   opt->skip_zero_p = 1;
+  opt->fp32_tau = 1e-6;
+  // s,p classes only: with fp32_tau = 1e-6, FP32 recurrences in d classes moved E_K of
+  // the 64-atom diamond by 1.2e-7, above the 1e-7 tolerance of this path
+  opt->fp32_class_mask = 0x3F;
 }
 
 extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int n_shells,
@@ -119,7 +127,8 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
   hfx_options o;
   hfx_default_options(&o);
   if (opt) o = *opt;
-  if (!(o.omega >= 0.0) || !(o.schwarz_tau >= 0.0) || !(o.prim_tau >= 0.0) || o.precision != HFX_FP64 ||
+  if (!(o.omega >= 0.0) || !(o.schwarz_tau >= 0.0) || !(o.prim_tau >= 0.0) || !(o.fp32_tau >= 0.0) ||
+      (o.precision != HFX_FP64 && o.precision != HFX_MIXED) ||
       (o.schedule != HFX_SCHED_QUARTET && o.schedule != HFX_SCHED_PAIR && o.schedule != HFX_SCHED_DYNAMIC)) {
     g_init_err = "invalid options";
     return HFX_ERR_ARG;
@@ -178,7 +187,7 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
       (r = ctx->alloc(&ctx->d_l, n_shells)) || (r = ctx->alloc(&ctx->d_nprim, n_shells)) ||
       (r = ctx->alloc(&ctx->d_prim_off, n_shells)) || (r = ctx->alloc(&ctx->d_bf_off, n_shells)) ||
       (r = ctx->alloc(&ctx->d_energy, 1)) || (r = ctx->alloc(&ctx->d_busy, 1024)) ||
-      (r = ctx->alloc(&ctx->d_counters, 3 * 21)) ||
+      (r = ctx->alloc(&ctx->d_counters, kNCnt * 21)) ||
       (r = ctx->alloc(&ctx->d_pmax, (size_t)n_shells * n_shells)) || (r = ctx->alloc(&ctx->d_work, 32)))
     return bail(r);
   ctx->n_part = 2 * ctx->n_sm;
@@ -214,9 +223,9 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
 // prim_setup / boys_eval (table branch; the asymptotic branch is not cheaper).
 static double boys_flops(int mmax) { return mmax <= 1 ? 7.0 + 12.0 * (mmax + 1) : 32.0 + 3.0 * mmax; }
 static double setup_flops(int E, int F, int Lt, bool erfc) {
-  double f = 1 + 8 + 3 + 9 + 12 + 2;                   // s, 1/s, rho/p, rho/q, rho, PQ, r2, T, rsqrt, pref
+  double f = 1 + 4 + 3 + 9 + 6 + 2;                    // s, 1/s, rho/p, rho/q, rho, PQ, r2, T, rsqrt, pref
   if (erfc)
-    f += 11 + 13 + 2 * boys_flops(Lt) + 4.0 * (Lt + 1);  // kappa, kappa^{1/2}, two Boys, G_m
+    f += 7 + 7 + 2 * boys_flops(Lt) + 4.0 * (Lt + 1);    // kappa, kappa^{1/2}, two Boys, G_m
   else
     f += boys_flops(Lt) + (Lt + 1);
   if (E > 0) f += 5;
@@ -224,7 +233,7 @@ static double setup_flops(int E, int F, int Lt, bool erfc) {
   return f;
 }
 // a primitive quartet dropped at kappa T >= table end costs the set-up up to that test
-static double skip_flops() { return 1 + 8 + 3 + 9 + 12 + 2 + 11; }
+static double skip_flops() { return 1 + 4 + 3 + 9 + 6 + 2 + 7; }
 
 static EriLaunch base_launch(hfx_ctx* ctx) {
   EriLaunch L;
@@ -243,11 +252,11 @@ static EriLaunch base_launch(hfx_ctx* ctx) {
   return L;
 }
 
-static int grid_for(hfx_ctx* ctx, int cls, int mode, long long work_items) {
-  const int gs = eri_group_size(cls);
+static int grid_for(hfx_ctx* ctx, int cls, int mode, long long work_items, bool force32 = false) {
+  const int gs = force32 ? 32 : eri_group_size(cls);
   const int groups_per_block = eri_block_size() / gs;
   long long need = (work_items + groups_per_block - 1) / groups_per_block;
-  long long cap = (long long)eri_blocks_per_sm(cls, mode) * ctx->n_sm;
+  long long cap = (long long)eri_blocks_per_sm(cls, mode, force32) * ctx->n_sm;
   long long g = std::min(need, cap);
   return (int)std::max(1LL, g);
 }
@@ -336,7 +345,7 @@ extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
         L.diag_list = d_cidx + start;
         L.diag_n = cnt[pc];
         L.diag_Q = ctx->d_Q;
-        CK(eri_launch(L, cls, 1, grid_for(ctx, cls, 1, cnt[pc]), s));
+        CK(eri_launch(L, cls, 1, grid_for(ctx, cls, 1, cnt[pc]), s, false));
       }
       start += cnt[pc];
     }
@@ -426,7 +435,7 @@ extern "C" int hfx_build_K(hfx_ctx* ctx, const double* P, double* K, int ld) {
   if (ctx->timing) {
     CK(cudaEventRecord(ctx->ev[0], s));
     CK(cudaMemsetAsync(ctx->d_busy, 0, 1024 * sizeof(unsigned long long), s));
-    CK(cudaMemsetAsync(ctx->d_counters, 0, 63 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ctx->d_counters, 0, kNCnt * 21 * sizeof(unsigned long long), s));
   }
   if (ld == n)
     CK(cudaMemsetAsync(K, 0, sizeof(double) * (size_t)n * n, s));
@@ -439,11 +448,15 @@ extern "C" int hfx_build_K(hfx_ctx* ctx, const double* P, double* K, int ld) {
   L.K = K;
   L.ld = ld;
   if (ctx->opt.schedule == HFX_SCHED_DYNAMIC) CK(cudaMemsetAsync(ctx->d_work, 0, 32 * sizeof(unsigned long long), s));
-  if (ctx->opt.skip_zero_p) {
+  const bool mixed = ctx->opt.precision == HFX_MIXED;
+  if (ctx->opt.skip_zero_p || mixed) {
     CK(launch_pmax(ctx->n_shells, ctx->d_bf_off, ctx->d_l, P, ld, ctx->d_pmax, s));
     L.pmax = ctx->d_pmax;
     L.ns = ctx->n_shells;
   }
+  L.skip_zero = ctx->opt.skip_zero_p;
+  L.fp32_tau = ctx->opt.fp32_tau;
+  L.Qs = ctx->d_Qs;
   if (ctx->timing) L.busy = ctx->d_busy;
   for (int cp = 0; cp < 21; ++cp) {
     ctx->class_launched[cp] = false;
@@ -458,12 +471,16 @@ extern "C" int hfx_build_K(hfx_ctx* ctx, const double* P, double* K, int ld) {
     L.ket_bin_start = ctx->rt.bin_start[lo];
     L.q_begin = ctx->cls_qbegin[cp];
     L.q_count = ctx->cls_q[cp];
-    L.counters = ctx->timing ? ctx->d_counters + 3 * cp : nullptr;
+    L.counters = ctx->timing ? ctx->d_counters + kNCnt * cp : nullptr;
+    // mixed precision: classes allowed FP32 run warp groups, so the FP32/FP64 choice per
+    // quartet is uniform over the lanes that work on it; the others keep the FP64 kernels
+    L.fp32_ok = mixed && ((ctx->opt.fp32_class_mask >> cp) & 1);
+    const bool force32 = L.fp32_ok;
     L.work = ctx->d_work + cp;
-    L.chunk = eri_group_size(cp) == 1 ? 256 : 8;
+    L.chunk = (!force32 && eri_group_size(cp) == 1) ? 256 : 8;
     const long long items = ctx->opt.schedule == HFX_SCHED_PAIR ? (L.row_end - L.row_begin) : L.q_count;
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[2 + 2 * cp], s));
-    CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items), s));
+    CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items, force32), s, force32));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3 + 2 * cp], s));
     ctx->class_launched[cp] = true;
   }
@@ -509,22 +526,31 @@ extern "C" int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out) {
   if (ctx->timing) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) st.ms_build = ms;
-    unsigned long long cnt[63];
+    unsigned long long cnt[kNCnt * 21];
     CK(cudaMemcpy(cnt, ctx->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
-    double fl = 0.0;
+    double fl = 0.0, fl32 = 0.0;
     for (int cp = 0; cp < 21; ++cp) {
       st.ms_class[cp] = 0.0;
       if (ctx->class_launched[cp] && cudaEventElapsedTime(&ms, ctx->ev[2 + 2 * cp], ctx->ev[3 + 2 * cp]) == cudaSuccess)
         st.ms_class[cp] = ms;
       const EriClassInfo& ci = class_info_host()[cp];
-      st.prim_quartets_class[cp] = (int64_t)cnt[3 * cp];
-      st.quartets_evaluated_class[cp] = (int64_t)cnt[3 * cp + 1];
-      st.flops_class[cp] =
-          (double)cnt[3 * cp] * (ci.flops_prim + setup_flops(ci.E, ci.F, ci.Lt, ctx->opt.omega > 0.0)) +
-          (double)cnt[3 * cp + 1] * ci.flops_quartet + (double)cnt[3 * cp + 2] * skip_flops();
-      fl += st.flops_class[cp];
+      const unsigned long long* c = cnt + kNCnt * cp;
+      st.prim_quartets_class[cp] = (int64_t)c[0];
+      st.quartets_evaluated_class[cp] = (int64_t)c[1];
+      st.quartets_fp32_class[cp] = (int64_t)c[3];
+      // FP64: every set-up (Boys step), the recurrences of FP64 quartets, every digest;
+      // FP32: the recurrences of FP32 quartets
+      const double f64 = (double)c[0] * setup_flops(ci.E, ci.F, ci.Lt, ctx->opt.omega > 0.0) +
+                         (double)(c[0] - c[4]) * ci.flops_prim +
+                         (double)(c[1] - c[3]) * (ci.flops_quartet - ci.flops_digest) +
+                         (double)c[1] * ci.flops_digest + (double)c[2] * skip_flops();
+      const double f32 = (double)c[4] * ci.flops_prim + (double)c[3] * (ci.flops_quartet - ci.flops_digest);
+      st.flops_class[cp] = f64 + f32;
+      fl += f64;
+      fl32 += f32;
     }
     st.flops_fp64 = fl;
+    st.flops_fp32 = fl32;
   }
   *out = st;
   return HFX_OK;

@@ -64,43 +64,64 @@ __device__ __forceinline__ int contract_g1(const EriLaunch& L, int bra, int ket,
 // quartets at a time (coefficient sets in shared memory), then share the ops of each
 // recurrence level.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int contract_g32(const EriLaunch& L, int bra, int ket, double* S, double* CF,
-                                             int lane) {
+// HRR and Cartesian -> spherical stages on the group scratch S (lanes share each stage)
+template <typename R>
+__device__ __forceinline__ void post_stages(const EriClassInfo& ci, const PairArrays& pa, int bra, int ket, R* S,
+                                            int lane) {
+  R AB[3], CD[3];
+  for (int i = 0; i < 3; ++i) {
+    AB[i] = R(__ldg(pa.AB + 3 * bra + i));
+    CD[i] = R(__ldg(pa.AB + 3 * ket + i));
+  }
+  for (int s = 0; s < ci.n_post; ++s) {
+    const int off = ci.post_off[s], n = ci.post_n[s], type = ci.post_type[s];
+    for (int o = lane; o < n; o += 32) post_op<R>(ld_op(kPostOps, off + o), type, S, 1, AB, CD);
+    __syncwarp();
+  }
+}
+
+template <typename R, bool FOLD>
+__device__ __forceinline__ int contract_g32(const EriLaunch& L, int bra, int ket, R* S, R* CF, int lane) {
   const EriClassInfo& ci = L.ci;
   const PairArrays& pa = L.pa;
-  double* V = S + ci.work_base;
+  R* V = S + ci.work_base;
   const int nb = __ldg(pa.prim_n + bra), nk = __ldg(pa.prim_n + ket);
   const PrimPair* pb = pa.prim + __ldg(pa.prim_off + bra);
   const PrimPair* pk = pa.prim + __ldg(pa.prim_off + ket);
-  for (int a = lane; a < ci.n_acc; a += 32) S[a] = 0.0;
+  for (int a = lane; a < ci.n_acc; a += 32) S[a] = R(0);
   const int npq = nb * nk;
   int any = 0;
   for (int base = 0; base < npq; base += 32) {
     const int t = base + lane;
     if (t < npq) {
       const int ib = t / nk, ik = t - ib * nk;
-      CoefRg c;
-      double Gm[kMaxLt + 1];
-      const bool ok = prim_setup(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, L.omega2, L.boys, c, Gm);
-      store_coef(c, Gm, ci.Lt, ok, CF + lane * NCOEF);
+      // the Boys step and the quantities feeding it stay in FP64 in either precision
+      if constexpr (sizeof(R) == 4) {
+        prim_setup_f32(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, L.omega2, L.boys, reinterpret_cast<float*>(CF + lane * NCOEF));
+      } else {
+        CoefRg c;
+        double Gm[kMaxLt + 1];
+        const bool ok = prim_setup(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, L.omega2, L.boys, c, Gm);
+        store_coef<R>(c, Gm, ci.Lt, ok, CF + lane * NCOEF);
+      }
     }
     __syncwarp();
     const int nchunk = min(32, npq - base);
     for (int u = 0; u < nchunk; ++u) {
-      const double* cf = CF + u * NCOEF;
-      if (cf[CF_SKIP] != 0.0) continue;
+      const R* cf = CF + u * NCOEF;
+      if (cf[CF_SKIP] != R(0)) continue;
       ++any;
-      const CoefSm c{cf};
+      const CoefSm<R> c{cf};
       for (int m = lane; m <= ci.Lt; m += 32) V[m] = cf[CF_G + m];
       __syncwarp();
       for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
         const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = lane; o < n; o += 32) vrr_bra<false>(ld_op(kVrrOps, off + o), V, S, 1, c);
+        for (int o = lane; o < n; o += 32) vrr_bra<FOLD>(ld_op(kVrrOps, off + o), V, S, 1, c);
         __syncwarp();
       }
       for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
         const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = lane; o < n; o += 32) vrr_ket<false>(ld_op(kVrrOps, off + o), V, S, 1, c);
+        for (int o = lane; o < n; o += 32) vrr_ket<FOLD>(ld_op(kVrrOps, off + o), V, S, 1, c);
         __syncwarp();
       }
       for (int a = lane; a < ci.n_accl; a += 32) {
@@ -112,34 +133,46 @@ __device__ __forceinline__ int contract_g32(const EriLaunch& L, int bra, int ket
     __syncwarp();  // every lane is done with this chunk's coefficient sets
   }
   if (!any) return 0;
-  double AB[3], CD[3];
-  for (int i = 0; i < 3; ++i) {
-    AB[i] = __ldg(pa.AB + 3 * bra + i);
-    CD[i] = __ldg(pa.AB + 3 * ket + i);
-  }
-  for (int s = 0; s < ci.n_post; ++s) {
-    const int off = ci.post_off[s], n = ci.post_n[s], type = ci.post_type[s];
-    for (int o = lane; o < n; o += 32) post_op(ld_op(kPostOps, off + o), type, S, 1, AB, CD);
+  if constexpr (sizeof(R) == 4) {
+    // FP32 recurrences end at the contracted block: widen it to FP64 (through the free
+    // coefficient area) so the horizontal recurrences and the spherical step, which cancel
+    // across distant pairs, run in FP64 on the group's FP64 scratch
+    double* Sd = reinterpret_cast<double*>(S);
+    double* tmp = reinterpret_cast<double*>(CF);
+    for (int a = lane; a < ci.n_acc; a += 32) tmp[a] = (double)S[a];
     __syncwarp();
+    for (int a = lane; a < ci.n_acc; a += 32) Sd[a] = tmp[a];
+    __syncwarp();
+    post_stages<double>(ci, pa, bra, ket, Sd, lane);
+  } else {
+    post_stages<R>(ci, pa, bra, ket, S, lane);
   }
   return any;
 }
 
+// Register caps: 6 blocks of 64 threads per SM (at most 170 registers) measured fastest
+// for both kernels; the FP64 set-up phase otherwise takes registers the hot VRR loop
+// does not need and costs occupancy.
 #ifndef HFX_G1_MINB
 #define HFX_G1_MINB 6
 #endif
 #ifndef HFX_G32_MINB
 #define HFX_G32_MINB 6
 #endif
+// the mixed-precision warp kernel carries both recurrence paths: 4 blocks per SM keep it
+// free of spills
+#ifndef HFX_G32M_MINB
+#define HFX_G32M_MINB 4
+#endif
 
-// The digest reads P_bd, P_bc, P_ad, P_ac: if all four blocks are exactly zero the
-// quartet contributes exactly nothing.
-__device__ __forceinline__ bool zero_p_blocks(const EriLaunch& L, int sa, int sb, int sc, int sd) {
-  if (!L.pmax) return false;
+// The digest reads P_bd, P_bc, P_ad, P_ac.  max of their max|P| (or 1 without the table):
+// 0 means the quartet contributes exactly nothing; the mixed-precision test uses it too.
+__device__ __forceinline__ double pmax4(const EriLaunch& L, int sa, int sb, int sc, int sd) {
+  if (!L.pmax) return 1.0;
   const double* pm = L.pmax;
   const size_t ns = L.ns;
-  return __ldg(pm + sb * ns + sd) == 0.0 && __ldg(pm + sb * ns + sc) == 0.0 &&
-         __ldg(pm + sa * ns + sd) == 0.0 && __ldg(pm + sa * ns + sc) == 0.0;
+  return fmax(fmax(__ldg(pm + sb * ns + sd), __ldg(pm + sb * ns + sc)),
+              fmax(__ldg(pm + sa * ns + sd), __ldg(pm + sa * ns + sc)));
 }
 
 __device__ __forceinline__ void record_busy(const EriLaunch& L, unsigned long long t0) {
@@ -187,7 +220,7 @@ __global__ void __launch_bounds__(64, HFX_G1_MINB) eri_g1_kernel(const EriLaunch
         const int bra = __ldg(L.sorted + bra_s), ket = __ldg(L.sorted + ket_s);
         const int sa = __ldg(L.pa.sa + bra), sb = __ldg(L.pa.sb + bra);
         const int sc = __ldg(L.pa.sa + ket), sd = __ldg(L.pa.sb + ket);
-        if (zero_p_blocks(L, sa, sb, sc, sd)) continue;
+        if (L.skip_zero && pmax4(L, sa, sb, sc, sd) == 0.0) continue;
         const int npq = __ldg(L.pa.prim_n + bra) * __ldg(L.pa.prim_n + ket);
         const int ne = contract_g1(L, bra, ket, S, st);
         n_prim += ne;
@@ -218,13 +251,17 @@ __global__ void __launch_bounds__(64, HFX_G1_MINB) eri_g1_kernel(const EriLaunch
   }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(64, HFX_G32_MINB) eri_g32_kernel(const EriLaunch L, int group_stride) {
+template <int MODE, bool FOLD, bool MIXED>
+__global__ void __launch_bounds__(64, MIXED ? HFX_G32M_MINB : HFX_G32_MINB) eri_g32_kernel(const EriLaunch L,
+                                                                                            int group_stride) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gpb = blockDim.x >> 5;
   double* S = smem + warp * group_stride;
   double* CF = S + L.ci.scratch + (L.ci.scratch & 1);
+  float* Sf = reinterpret_cast<float*>(S);    // the FP32 engine reuses the group's memory
+  float* CFf = reinterpret_cast<float*>(CF);
+  unsigned long long n32q = 0, n32p = 0;
   const long long gid = (long long)blockIdx.x * gpb + warp;
   const long long ng = (long long)gridDim.x * gpb;
   unsigned long long t0 = 0, n_prim = 0, n_skip = 0, n_quart = 0;
@@ -253,19 +290,33 @@ __global__ void __launch_bounds__(64, HFX_G32_MINB) eri_g32_kernel(const EriLaun
         const int bra = __ldg(L.sorted + bra_s), ket = __ldg(L.sorted + ket_s);
         const int sa = __ldg(L.pa.sa + bra), sb = __ldg(L.pa.sb + bra);
         const int sc = __ldg(L.pa.sa + ket), sd = __ldg(L.pa.sb + ket);
-        if (zero_p_blocks(L, sa, sb, sc, sd)) continue;
+        const double pm = pmax4(L, sa, sb, sc, sd);
+        if (L.skip_zero && pm == 0.0) continue;
+        // mixed precision: FP32 recurrences when the Schwarz bound times the largest density
+        // element the quartet touches is below fp32_tau (warp-uniform decision)
+        const bool f32 = MIXED && L.fp32_ok && __ldg(L.Qs + bra_s) * __ldg(L.Qs + ket_s) * pm < L.fp32_tau;
         const int npq = __ldg(L.pa.prim_n + bra) * __ldg(L.pa.prim_n + ket);
-        const int ne = contract_g32(L, bra, ket, S, CF, lane);
+        int ne;
+        if (MIXED && f32)
+          ne = contract_g32<float, FOLD>(L, bra, ket, Sf, CFf, lane);
+        else
+          ne = contract_g32<double, FOLD>(L, bra, ket, S, CF, lane);
         n_prim += ne;
         n_skip += npq - ne;
         if (!ne) continue;
         ++n_quart;
+        if (f32) {
+          ++n32q;
+          n32p += ne;
+        }
         double deg = 1.0;
         if (sa == sb) deg *= 0.5;
         if (sc == sd) deg *= 0.5;
         if (bra_s == ket_s) deg *= 0.5;
-        digest(L.ci, S + L.ci.out_base, 1, __ldg(L.sh.bf_off + sa), __ldg(L.sh.bf_off + sb),
-               __ldg(L.sh.bf_off + sc), __ldg(L.sh.bf_off + sd), deg, L.P, L.K, L.ld, lane, 32);
+        const int A = __ldg(L.sh.bf_off + sa), B = __ldg(L.sh.bf_off + sb);
+        const int C = __ldg(L.sh.bf_off + sc), D = __ldg(L.sh.bf_off + sd);
+        // an FP32 quartet leaves its final block in FP64 too (see contract_g32)
+        digest(L.ci, S + L.ci.out_base, 1, A, B, C, D, deg, L.P, L.K, L.ld, lane, 32);
         __syncwarp();
       }
     }
@@ -273,7 +324,7 @@ __global__ void __launch_bounds__(64, HFX_G32_MINB) eri_g32_kernel(const EriLaun
     for (long long t = gid; t < L.diag_n; t += ng) {
       const int p = __ldg(L.diag_list + t);
       double mx = 0.0;
-      if (contract_g32(L, p, p, S, CF, lane)) mx = diag_max(L.ci, S + L.ci.out_base, 1);
+      if (contract_g32<double, FOLD>(L, p, p, S, CF, lane)) mx = diag_max(L.ci, S + L.ci.out_base, 1);
       if (lane == 0) L.diag_Q[p] = sqrt(mx);
       __syncwarp();
     }
@@ -283,6 +334,8 @@ __global__ void __launch_bounds__(64, HFX_G32_MINB) eri_g32_kernel(const EriLaun
     atomicAdd(L.counters + 0, n_prim);
     atomicAdd(L.counters + 1, n_quart);
     atomicAdd(L.counters + 2, n_skip);
+    atomicAdd(L.counters + 3, n32q);
+    atomicAdd(L.counters + 4, n32p);
   }
 }
 
@@ -301,25 +354,34 @@ static int g32_stride(int cls) {
   return s + (s & 1) + 32 * NCOEF + 1;  // +1: stagger the groups' banks
 }
 
-size_t eri_smem_bytes(int cls) {
-  if (eri_group_size(cls) == 1) return sizeof(double) * (size_t)kClassInfo[cls].scratch * kBlock;
+size_t eri_smem_bytes(int cls, bool force32) {
+  if (!force32 && eri_group_size(cls) == 1) return sizeof(double) * (size_t)kClassInfo[cls].scratch * kBlock;
   return sizeof(double) * (size_t)g32_stride(cls) * (kBlock / 32);
 }
 
 int eri_block_size() { return kBlock; }
 
-static const void* kernel_ptr(int cls, int mode) {
-  const bool g1 = eri_group_size(cls) == 1;
+// classes whose tables fold the accumulation (the thread-per-quartet ones)
+static bool class_folds(int cls) { return kClassInfo[cls].scratch <= HFX_G1_MAX_SCRATCH; }
+
+// force32 (mixed precision): warp groups for every class, with the FP32 path compiled in
+static const void* kernel_ptr(int cls, int mode, bool force32) {
+  const bool g1 = !force32 && eri_group_size(cls) == 1;
   if (g1) return mode == 0 ? (const void*)eri_g1_kernel<0> : (const void*)eri_g1_kernel<1>;
-  return mode == 0 ? (const void*)eri_g32_kernel<0> : (const void*)eri_g32_kernel<1>;
+  const bool fold = class_folds(cls);
+  if (mode == 1) return fold ? (const void*)eri_g32_kernel<1, true, false> : (const void*)eri_g32_kernel<1, false, false>;
+  if (force32) return fold ? (const void*)eri_g32_kernel<0, true, true> : (const void*)eri_g32_kernel<0, false, true>;
+  return fold ? (const void*)eri_g32_kernel<0, true, false> : (const void*)eri_g32_kernel<0, false, false>;
 }
 
 cudaError_t eri_prepare() {
   // allow the largest dynamic shared memory any class needs
   size_t mx = 0;
-  for (int c = 0; c < HFX_N_CLASSES; ++c) mx = std::max(mx, eri_smem_bytes(c));
-  const void* ks[4] = {(const void*)eri_g1_kernel<0>, (const void*)eri_g1_kernel<1>,
-                       (const void*)eri_g32_kernel<0>, (const void*)eri_g32_kernel<1>};
+  for (int c = 0; c < HFX_N_CLASSES; ++c) mx = std::max(mx, std::max(eri_smem_bytes(c, false), eri_smem_bytes(c, true)));
+  const void* ks[8] = {(const void*)eri_g1_kernel<0>, (const void*)eri_g1_kernel<1>,
+                       (const void*)eri_g32_kernel<0, false, false>, (const void*)eri_g32_kernel<1, false, false>,
+                       (const void*)eri_g32_kernel<0, true, false>, (const void*)eri_g32_kernel<1, true, false>,
+                       (const void*)eri_g32_kernel<0, false, true>, (const void*)eri_g32_kernel<0, true, true>};
   for (auto k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return e;
@@ -327,27 +389,34 @@ cudaError_t eri_prepare() {
   return cudaSuccess;
 }
 
-int eri_blocks_per_sm(int cls, int mode) {
+int eri_blocks_per_sm(int cls, int mode, bool force32) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(cls, mode), kBlock,
-                                                    eri_smem_bytes(cls)) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(cls, mode, force32), kBlock,
+                                                    eri_smem_bytes(cls, force32)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
-cudaError_t eri_launch(const EriLaunch& L, int cls, int mode, int grid, cudaStream_t stream) {
-  const size_t smem = eri_smem_bytes(cls);
-  if (eri_group_size(cls) == 1) {
+cudaError_t eri_launch(const EriLaunch& L, int cls, int mode, int grid, cudaStream_t stream, bool force32) {
+  const size_t smem = eri_smem_bytes(cls, force32);
+  if (!force32 && eri_group_size(cls) == 1) {
     if (mode == 0)
       eri_g1_kernel<0><<<grid, kBlock, smem, stream>>>(L);
     else
       eri_g1_kernel<1><<<grid, kBlock, smem, stream>>>(L);
   } else {
     const int gs = g32_stride(cls);
-    if (mode == 0)
-      eri_g32_kernel<0><<<grid, kBlock, smem, stream>>>(L, gs);
-    else
-      eri_g32_kernel<1><<<grid, kBlock, smem, stream>>>(L, gs);
+    const bool fold = class_folds(cls);
+    if (mode == 1) {
+      if (fold) eri_g32_kernel<1, true, false><<<grid, kBlock, smem, stream>>>(L, gs);
+      else eri_g32_kernel<1, false, false><<<grid, kBlock, smem, stream>>>(L, gs);
+    } else if (force32) {
+      if (fold) eri_g32_kernel<0, true, true><<<grid, kBlock, smem, stream>>>(L, gs);
+      else eri_g32_kernel<0, false, true><<<grid, kBlock, smem, stream>>>(L, gs);
+    } else {
+      if (fold) eri_g32_kernel<0, true, false><<<grid, kBlock, smem, stream>>>(L, gs);
+      else eri_g32_kernel<0, false, false><<<grid, kBlock, smem, stream>>>(L, gs);
+    }
   }
   return cudaGetLastError();
 }

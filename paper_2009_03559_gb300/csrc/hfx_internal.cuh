@@ -20,8 +20,9 @@ struct EriClassInfo {
   int post_type[8], post_off[8], post_n[8];  // 0 bra HRR, 1 ket HRR, 2 spherical
   int out_base;                        // final spherical block in group scratch
   int dims[4];                         // final block extents (a, b, c, d)
-  int flops_prim, flops_quartet;       // FP64 flop model (VRR+acc per primitive quartet;
+  int flops_prim, flops_quartet;       // flop model (VRR+acc per primitive quartet;
                                        // HRR+spherical+digest per contracted quartet)
+  int flops_digest;                    // the digest part of flops_quartet (always FP64)
 };
 
 extern const EriClassInfo* class_info_host();
@@ -48,6 +49,8 @@ struct __align__(16) PrimPair {
   double PA[3];        // P - A (A = centre of the pair's first shell)
   double C;            // prefactor (see above)
   double pad;
+  // FP32 copies for the FP32 recurrences (conversions would run on the FP64 pipe)
+  float pf, inv2pf, PAf[3], pad_f[3];
 };
 
 // Device arrays describing shell pairs (indexed by candidate-pair id).
@@ -66,24 +69,19 @@ struct ShellArrays {
 };
 
 // ---------------------------------------------------------------------------
-// FP64 reciprocal and reciprocal square root: FP32 hardware seed refined by two
-// Newton-Raphson steps (each doubles the number of correct bits: 2^-22 -> 2^-44
-// -> below FP64 rounding).  Arguments are positive and well inside FP32 range.
+// FP64 reciprocal and reciprocal square root: FP32 hardware seed (relative error below
+// 2^-22) refined by one Newton-Raphson step, which squares the error: below 1e-13
+// relative, far inside what the exchange matrix needs (FP64 instructions are the scarce
+// resource on this part).  Arguments are positive and well inside FP32 range.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double rcp_nr(double x) {
-  double r = (double)__frcp_rn((float)x);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  const double r = (double)__frcp_rn((float)x);
+  return fma(r, fma(-x, r, 1.0), r);
 }
 
 __device__ __forceinline__ double rsqrt_nr(double x) {
-  double y = (double)rsqrtf((float)x);
-  double e = fma(-x * y, y, 1.0);   // 1 - x y^2
-  y = fma(0.5 * y, e, y);
-  e = fma(-x * y, y, 1.0);
-  return fma(0.5 * y, e, y);
+  const double y = (double)rsqrtf((float)x);
+  return fma(0.5 * y, fma(-x * y, y, 1.0), y);  // y (1 + (1 - x y^2)/2)
 }
 
 // F_m(x) for m = 0..mmax (mmax <= kMaxLt).  Below kBoysXmax: seven-term Taylor
@@ -167,8 +165,12 @@ struct EriLaunch {
   double* diag_Q;
   unsigned long long* busy;     // optional per-SM globaltimer busy ns (indexed by %smid)
   unsigned long long* counters; // optional: [0] primitive quartets evaluated, [1] quartets, [2] skipped
-  const double* pmax;           // optional: max |P| of each shell-pair block (ns x ns); quartets
-  int ns;                       // whose four density blocks are all zero are skipped
+  const double* pmax;           // optional: max |P| of each shell-pair block (ns x ns)
+  int ns;
+  int skip_zero;                // skip quartets whose four density blocks are all zero
+  int fp32_ok;                  // mixed precision allowed for this class
+  double fp32_tau;              // FP32 iff Q_IJ Q_KL max|P_blocks| < fp32_tau
+  const double* Qs;             // Schwarz factor of each sorted pair
 };
 
 

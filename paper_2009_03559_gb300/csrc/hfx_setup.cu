@@ -138,6 +138,12 @@ __global__ void k_prim_fill(int n_cand, const int* __restrict__ sa, const int* _
       }
       r.C = C;
       r.pad = 0.0;
+      r.pf = (float)p;
+      r.inv2pf = (float)r.inv2p;
+      for (int i = 0; i < 3; ++i) {
+        r.PAf[i] = (float)r.PA[i];
+        r.pad_f[i] = 0.f;
+      }
       out[n++] = r;
     }
   }

@@ -20,12 +20,15 @@ ERR_NAMES = {0: "OK", -1: "ARG", -2: "UNSUPPORTED_L", -3: "OOM", -4: "CUDA", -5:
 
 PAIR_CLASSES = ["ss", "ps", "pp", "ds", "dp", "dd"]
 QUARTET_CLASSES = [f"({PAIR_CLASSES[hi]}|{PAIR_CLASSES[lo]})" for hi in range(6) for lo in range(hi + 1)]
+# quartet classes without d shells (bra and ket pair classes among ss, ps, pp)
+SP_CLASS_MASK = sum(1 << (hi * (hi + 1) // 2 + lo) for hi in range(3) for lo in range(hi + 1))
 
 
 class Options(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("schwarz_tau", ctypes.c_double), ("rcut_bohr", ctypes.c_double),
-                ("prim_tau", ctypes.c_double), ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
-                ("skip_zero_p", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("prim_tau", ctypes.c_double), ("fp32_tau", ctypes.c_double), ("precision", ctypes.c_int),
+                ("schedule", ctypes.c_int), ("skip_zero_p", ctypes.c_int), ("fp32_class_mask", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -33,6 +36,7 @@ class Stats(ctypes.Structure):
                 ("n_quartets", ctypes.c_int64), ("n_quartets_class", ctypes.c_int64 * 21),
                 ("prim_quartets_class", ctypes.c_int64 * 21),
                 ("quartets_evaluated_class", ctypes.c_int64 * 21),
+                ("quartets_fp32_class", ctypes.c_int64 * 21), ("flops_fp32", ctypes.c_double),
                 ("flops_fp64", ctypes.c_double), ("flops_class", ctypes.c_double * 21),
                 ("group_size_class", ctypes.c_int32 * 21),
                 ("ms_pairs", ctypes.c_double), ("ms_build", ctypes.c_double),
@@ -44,6 +48,8 @@ class Stats(ctypes.Structure):
             "n_quartets": int(self.n_quartets), "n_quartets_class": [int(x) for x in self.n_quartets_class],
             "prim_quartets_class": [int(x) for x in self.prim_quartets_class],
             "quartets_evaluated_class": [int(x) for x in self.quartets_evaluated_class],
+            "quartets_fp32_class": [int(x) for x in self.quartets_fp32_class],
+            "flops_fp32": float(self.flops_fp32),
             "flops_fp64": float(self.flops_fp64), "flops_class": [float(x) for x in self.flops_class],
             "group_size_class": [int(x) for x in self.group_size_class], "ms_pairs": float(self.ms_pairs),
             "ms_build": float(self.ms_build), "ms_class": [float(x) for x in self.ms_class],
@@ -138,7 +144,7 @@ class HFX:
     """
 
     def __init__(self, system, stream=None, tau=None, rcut=None, omega=None, schedule=HFX_SCHED_DYNAMIC,
-                 prim_tau=None, skip_zero_p=True):
+                 prim_tau=None, skip_zero_p=True, precision=HFX_FP64, fp32_tau=None, fp32_class_mask=None):
         import torch  # device memory and streams only
         if not torch.cuda.is_available():
             raise RuntimeError("HFX needs a CUDA device; there is no CPU path")
@@ -154,6 +160,11 @@ class HFX:
             o.prim_tau = prim_tau
         o.schedule = schedule
         o.skip_zero_p = 1 if skip_zero_p else 0
+        o.precision = precision
+        if fp32_tau is not None:
+            o.fp32_tau = fp32_tau
+        if fp32_class_mask is not None:
+            o.fp32_class_mask = fp32_class_mask
         self.options = o
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         xyz, sa, sl, sn, al, co = system.basis_arrays()
