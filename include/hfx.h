@@ -172,6 +172,50 @@ const char* hfx_last_error(const hfx_ctx* ctx);
 /* Releases the context and all device memory it owns (synchronises the stream). */
 void hfx_free(hfx_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Batched K builds: the quartets of several systems (contexts with pair lists) go into
+ * one launch per angular class; the whole build (zeroing, density block maxima, the 21
+ * class launches, K = A + A^T, E_K per system) is captured once as a CUDA graph and
+ * replayed.  The systems' P and K pointers are read from a device table refreshed from
+ * host memory before each replay, so new buffers need no new graph.  Precision and
+ * zero-block skip follow the first context's options.
+ * ------------------------------------------------------------------------- */
+typedef struct hfx_batch hfx_batch;
+
+typedef struct {
+  int64_t n_quartets;          /* screened quartets of all systems */
+  double ms_last;              /* GPU time of the last hfx_batch_run (events around it) */
+  int32_t group_size_class[21];/* chosen lanes per quartet (1 or 32) per class */
+  int32_t chunk_class[21];     /* chosen quartets per dynamic claim per class */
+  double tune_ms_class[21];    /* best class-launch time seen by the tuner */
+} hfx_batch_stats;
+
+/* Creates a batch over n contexts (all with pair lists, same device).  Runs are ordered
+ * after earlier work on `stream` (NULL = the first context's stream) and later work on it
+ * waits for them; the batch captures and launches its graph on a stream of its own.  The
+ * contexts must outlive the batch. */
+int hfx_batch_create(hfx_batch** out, hfx_ctx* const* ctxs, int n, void* stream);
+
+/* Autotuner: for every class, times its batched launch with each candidate group size
+ * (1 or 32 lanes per quartet, where the class allows both) and dynamic chunk size, and
+ * keeps the fastest.  Uses P/K like hfx_batch_run (their K contents are overwritten by
+ * the tuning launches; run hfx_batch_run afterwards).  Synchronises. */
+int hfx_batch_tune(hfx_batch* b, const double* const* P_dev, double* const* K_dev, const int* ld);
+
+/* Builds K_s for P_s of every system s (device pointers; ld[s] >= n_bf of system s; ld
+ * may be NULL for ld = n_bf).  The first call captures the graph, later calls replay it.
+ * Asynchronous; E_K of system s lands in its context (hfx_energy). */
+int hfx_batch_run(hfx_batch* b, const double* const* P_dev, double* const* K_dev, const int* ld);
+
+/* 1 (default): capture and replay a CUDA graph; 0: plain launches every run. */
+int hfx_batch_set_graph(hfx_batch* b, int enable);
+
+int hfx_batch_get_stats(hfx_batch* b, hfx_batch_stats* out);
+void hfx_batch_free(hfx_batch* b);
+
+/* One-shot form: create a batch, run it once, free it. */
+int hfx_build_K_batched(hfx_ctx* const* ctxs, const double* const* P_dev, double* const* K_dev, const int* ld, int n);
+
 /* Largest matrix order accepted by hfx_energy_noalloc (rows of its fixed scratch). */
 #define HFX_NOALLOC_MAX_N 16384
 

@@ -183,58 +183,148 @@ __device__ __forceinline__ void record_busy(const EriLaunch& L, unsigned long lo
   }
 }
 
-template <int MODE>
+// Per-thread tallies of one kernel, added to the launch's counters once at the end.
+struct Tally {
+  unsigned long long prim = 0, quart = 0, skip = 0, q32 = 0, p32 = 0;
+};
+
+// Quartets [q0, q1) of the launch record Ls, G = 1: lane `lane` of the warp takes
+// q0 + lane, q0 + lane + 32, ... (neighbouring lanes on neighbouring quartets).
+__device__ __forceinline__ void g1_range(const EriLaunch& Ls, long long q0, long long q1, double* S, int st,
+                                         int lane, Tally& t) {
+  if (q0 + lane >= q1) return;
+  int r = find_row(Ls.qoff, Ls.row_begin, Ls.row_end, q0 + lane);
+  for (long long q = q0 + lane; q < q1; q += 32) {
+    while (__ldg(Ls.qoff + r + 1) <= q) ++r;
+    const int bra_s = Ls.bra_bin_start + (r - Ls.row_begin);
+    const int ket_s = Ls.ket_bin_start + (int)(q - __ldg(Ls.qoff + r));
+    const int bra = __ldg(Ls.sorted + bra_s), ket = __ldg(Ls.sorted + ket_s);
+    const int sa = __ldg(Ls.pa.sa + bra), sb = __ldg(Ls.pa.sb + bra);
+    const int sc = __ldg(Ls.pa.sa + ket), sd = __ldg(Ls.pa.sb + ket);
+    if (Ls.skip_zero && pmax4(Ls, sa, sb, sc, sd) == 0.0) continue;
+    const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
+    const int ne = contract_g1(Ls, bra, ket, S, st);
+    t.prim += ne;
+    t.skip += npq - ne;
+    if (!ne) continue;
+    ++t.quart;
+    double deg = 1.0;
+    if (sa == sb) deg *= 0.5;
+    if (sc == sd) deg *= 0.5;
+    if (bra_s == ket_s) deg *= 0.5;
+    digest(Ls.ci, S + Ls.ci.out_base * st, st, __ldg(Ls.sh.bf_off + sa), __ldg(Ls.sh.bf_off + sb),
+           __ldg(Ls.sh.bf_off + sc), __ldg(Ls.sh.bf_off + sd), deg, Ls.P, Ls.K, Ls.ld, 0, 1);
+  }
+}
+
+// Quartets [q0, q1) of the launch record Ls, G = 32: the warp takes them one by one.
+template <bool FOLD, bool MIXED>
+__device__ __forceinline__ void g32_range(const EriLaunch& Ls, long long q0, long long q1, double* S, double* CF,
+                                          int lane, Tally& t) {
+  float* Sf = reinterpret_cast<float*>(S);  // the FP32 engine reuses the group's memory
+  float* CFf = reinterpret_cast<float*>(CF);
+  if (q0 >= q1) return;
+  int r = find_row(Ls.qoff, Ls.row_begin, Ls.row_end, q0);
+  for (long long q = q0; q < q1; ++q) {
+    while (__ldg(Ls.qoff + r + 1) <= q) ++r;
+    const int bra_s = Ls.bra_bin_start + (r - Ls.row_begin);
+    const int ket_s = Ls.ket_bin_start + (int)(q - __ldg(Ls.qoff + r));
+    const int bra = __ldg(Ls.sorted + bra_s), ket = __ldg(Ls.sorted + ket_s);
+    const int sa = __ldg(Ls.pa.sa + bra), sb = __ldg(Ls.pa.sb + bra);
+    const int sc = __ldg(Ls.pa.sa + ket), sd = __ldg(Ls.pa.sb + ket);
+    const double pm = pmax4(Ls, sa, sb, sc, sd);
+    if (Ls.skip_zero && pm == 0.0) continue;
+    // mixed precision: FP32 recurrences when the Schwarz bound times the largest density
+    // element the quartet touches is below fp32_tau (warp-uniform decision)
+    const bool f32 = MIXED && Ls.fp32_ok && __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pm < Ls.fp32_tau;
+    const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
+    int ne;
+    if (MIXED && f32)
+      ne = contract_g32<float, FOLD>(Ls, bra, ket, Sf, CFf, lane);
+    else
+      ne = contract_g32<double, FOLD>(Ls, bra, ket, S, CF, lane);
+    t.prim += ne;
+    t.skip += npq - ne;
+    if (!ne) continue;
+    ++t.quart;
+    if (f32) {
+      ++t.q32;
+      t.p32 += ne;
+    }
+    double deg = 1.0;
+    if (sa == sb) deg *= 0.5;
+    if (sc == sd) deg *= 0.5;
+    if (bra_s == ket_s) deg *= 0.5;
+    const int A = __ldg(Ls.sh.bf_off + sa), B = __ldg(Ls.sh.bf_off + sb);
+    const int C = __ldg(Ls.sh.bf_off + sc), D = __ldg(Ls.sh.bf_off + sd);
+    // an FP32 quartet leaves its final block in FP64 too (see contract_g32)
+    digest(Ls.ci, S + Ls.ci.out_base, 1, A, B, C, D, deg, Ls.P, Ls.K, Ls.ld, lane, 32);
+    __syncwarp();
+  }
+}
+
+// The quartet ranges a warp works on.  Static schedules: one range (group_range).
+// Dynamic: chunks claimed from the launch's device counter.  Batched (L.n_sys > 0): chunks
+// of the systems' concatenated quartet lists; a chunk is split at system boundaries
+// (L.seg[s] = first index of system s) and each part runs with that system's record.
+template <bool BATCH, class F>
+__device__ __forceinline__ void for_each_range(const EriLaunch& L, long long wid, long long nw, int lane, F&& f) {
+  if (!BATCH && L.schedule != 2) {
+    long long q0, q1;
+    group_range(L, wid, nw, q0, q1);
+    f(L, q0, q1);
+    return;
+  }
+  const long long total = L.q_count;
+  while (true) {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(L.work, (unsigned long long)L.chunk);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    long long c0 = (long long)c;
+    if (c0 >= total) break;
+    const long long c1 = min(c0 + L.chunk, total);
+    if constexpr (!BATCH) {
+      f(L, L.q_begin + c0, L.q_begin + c1);
+      continue;
+    }
+    while (c0 < c1) {
+      int lo = 0, hi = L.n_sys - 1;  // last s with seg[s] <= c0
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(L.seg + mid) <= c0) lo = mid; else hi = mid - 1;
+      }
+      const long long e = min(c1, __ldg(L.seg + lo + 1));
+      const EriLaunch& Ls = L.batch[lo];
+      f(Ls, Ls.q_begin + (c0 - __ldg(L.seg + lo)), Ls.q_begin + (e - __ldg(L.seg + lo)));
+      c0 = e;
+    }
+  }
+}
+
+__device__ __forceinline__ void flush_tally(const EriLaunch& L, const Tally& t) {
+  if (!L.counters) return;
+  atomicAdd(L.counters + 0, t.prim);
+  atomicAdd(L.counters + 1, t.quart);
+  atomicAdd(L.counters + 2, t.skip);
+  atomicAdd(L.counters + 3, t.q32);
+  atomicAdd(L.counters + 4, t.p32);
+}
+
+template <int MODE, bool BATCH>
 __global__ void __launch_bounds__(64, HFX_G1_MINB) eri_g1_kernel(const EriLaunch L) {
   extern __shared__ double smem[];
   const int st = blockDim.x;
   double* S = smem + threadIdx.x;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long ng = (long long)gridDim.x * blockDim.x;
-  unsigned long long t0 = 0, n_prim = 0, n_skip = 0, n_quart = 0;
+  unsigned long long t0 = 0;
   if (L.busy && threadIdx.x == 0) t0 = globaltimer_ns();
   if (MODE == 0) {
-    // a warp works on a range of the quartet list (an even share, or chunks claimed from
-    // the device counter); its lanes take interleaved quartets of the range, so
-    // neighbouring lanes work on neighbouring quartets
     const int lane = threadIdx.x & 31;
-    long long q0, q1;
-    bool more = true;
-    if (L.schedule != 2) group_range(L, gid >> 5, ng >> 5, q0, q1);
-    while (more) {
-      if (L.schedule == 2) {
-        unsigned long long c0 = 0;
-        if (lane == 0) c0 = atomicAdd(L.work, (unsigned long long)L.chunk);
-        c0 = __shfl_sync(0xffffffffu, c0, 0);
-        if ((long long)c0 >= L.q_count) break;
-        q0 = L.q_begin + (long long)c0;
-        q1 = min(q0 + L.chunk, L.q_begin + L.q_count);
-      } else {
-        more = false;
-      }
-      if (q0 + lane >= q1) continue;
-      int r = find_row(L.qoff, L.row_begin, L.row_end, q0 + lane);
-      for (long long q = q0 + lane; q < q1; q += 32) {
-        while (__ldg(L.qoff + r + 1) <= q) ++r;
-        const int bra_s = L.bra_bin_start + (r - L.row_begin);
-        const int ket_s = L.ket_bin_start + (int)(q - __ldg(L.qoff + r));
-        const int bra = __ldg(L.sorted + bra_s), ket = __ldg(L.sorted + ket_s);
-        const int sa = __ldg(L.pa.sa + bra), sb = __ldg(L.pa.sb + bra);
-        const int sc = __ldg(L.pa.sa + ket), sd = __ldg(L.pa.sb + ket);
-        if (L.skip_zero && pmax4(L, sa, sb, sc, sd) == 0.0) continue;
-        const int npq = __ldg(L.pa.prim_n + bra) * __ldg(L.pa.prim_n + ket);
-        const int ne = contract_g1(L, bra, ket, S, st);
-        n_prim += ne;
-        n_skip += npq - ne;
-        if (!ne) continue;
-        ++n_quart;
-        double deg = 1.0;
-        if (sa == sb) deg *= 0.5;
-        if (sc == sd) deg *= 0.5;
-        if (bra_s == ket_s) deg *= 0.5;
-        digest(L.ci, S + L.ci.out_base * st, st, __ldg(L.sh.bf_off + sa), __ldg(L.sh.bf_off + sb),
-               __ldg(L.sh.bf_off + sc), __ldg(L.sh.bf_off + sd), deg, L.P, L.K, L.ld, 0, 1);
-      }
-    }
+    Tally t;
+    for_each_range<BATCH>(L, gid >> 5, ng >> 5, lane,
+                          [&](const EriLaunch& Ls, long long q0, long long q1) { g1_range(Ls, q0, q1, S, st, lane, t); });
+    flush_tally(L, t);
   } else {
     for (long long t = gid; t < L.diag_n; t += ng) {
       const int p = __ldg(L.diag_list + t);
@@ -244,14 +334,9 @@ __global__ void __launch_bounds__(64, HFX_G1_MINB) eri_g1_kernel(const EriLaunch
     }
   }
   record_busy(L, t0);
-  if (L.counters && MODE == 0) {
-    atomicAdd(L.counters + 0, n_prim);
-    atomicAdd(L.counters + 1, n_quart);
-    atomicAdd(L.counters + 2, n_skip);
-  }
 }
 
-template <int MODE, bool FOLD, bool MIXED>
+template <int MODE, bool FOLD, bool MIXED, bool BATCH>
 __global__ void __launch_bounds__(64, MIXED ? HFX_G32M_MINB : HFX_G32_MINB) eri_g32_kernel(const EriLaunch L,
                                                                                             int group_stride) {
   extern __shared__ double smem[];
@@ -259,67 +344,16 @@ __global__ void __launch_bounds__(64, MIXED ? HFX_G32M_MINB : HFX_G32_MINB) eri_
   const int gpb = blockDim.x >> 5;
   double* S = smem + warp * group_stride;
   double* CF = S + L.ci.scratch + (L.ci.scratch & 1);
-  float* Sf = reinterpret_cast<float*>(S);    // the FP32 engine reuses the group's memory
-  float* CFf = reinterpret_cast<float*>(CF);
-  unsigned long long n32q = 0, n32p = 0;
   const long long gid = (long long)blockIdx.x * gpb + warp;
   const long long ng = (long long)gridDim.x * gpb;
-  unsigned long long t0 = 0, n_prim = 0, n_skip = 0, n_quart = 0;
+  unsigned long long t0 = 0;
   if (L.busy && threadIdx.x == 0) t0 = globaltimer_ns();
   if (MODE == 0) {
-    long long q0, q1;
-    bool more = true;
-    if (L.schedule != 2) group_range(L, gid, ng, q0, q1);
-    while (more) {
-      if (L.schedule == 2) {
-        unsigned long long c0 = 0;
-        if (lane == 0) c0 = atomicAdd(L.work, (unsigned long long)L.chunk);
-        c0 = __shfl_sync(0xffffffffu, c0, 0);
-        if ((long long)c0 >= L.q_count) break;
-        q0 = L.q_begin + (long long)c0;
-        q1 = min(q0 + L.chunk, L.q_begin + L.q_count);
-      } else {
-        more = false;
-      }
-      if (q0 >= q1) continue;
-      int r = find_row(L.qoff, L.row_begin, L.row_end, q0);
-      for (long long q = q0; q < q1; ++q) {
-        while (__ldg(L.qoff + r + 1) <= q) ++r;
-        const int bra_s = L.bra_bin_start + (r - L.row_begin);
-        const int ket_s = L.ket_bin_start + (int)(q - __ldg(L.qoff + r));
-        const int bra = __ldg(L.sorted + bra_s), ket = __ldg(L.sorted + ket_s);
-        const int sa = __ldg(L.pa.sa + bra), sb = __ldg(L.pa.sb + bra);
-        const int sc = __ldg(L.pa.sa + ket), sd = __ldg(L.pa.sb + ket);
-        const double pm = pmax4(L, sa, sb, sc, sd);
-        if (L.skip_zero && pm == 0.0) continue;
-        // mixed precision: FP32 recurrences when the Schwarz bound times the largest density
-        // element the quartet touches is below fp32_tau (warp-uniform decision)
-        const bool f32 = MIXED && L.fp32_ok && __ldg(L.Qs + bra_s) * __ldg(L.Qs + ket_s) * pm < L.fp32_tau;
-        const int npq = __ldg(L.pa.prim_n + bra) * __ldg(L.pa.prim_n + ket);
-        int ne;
-        if (MIXED && f32)
-          ne = contract_g32<float, FOLD>(L, bra, ket, Sf, CFf, lane);
-        else
-          ne = contract_g32<double, FOLD>(L, bra, ket, S, CF, lane);
-        n_prim += ne;
-        n_skip += npq - ne;
-        if (!ne) continue;
-        ++n_quart;
-        if (f32) {
-          ++n32q;
-          n32p += ne;
-        }
-        double deg = 1.0;
-        if (sa == sb) deg *= 0.5;
-        if (sc == sd) deg *= 0.5;
-        if (bra_s == ket_s) deg *= 0.5;
-        const int A = __ldg(L.sh.bf_off + sa), B = __ldg(L.sh.bf_off + sb);
-        const int C = __ldg(L.sh.bf_off + sc), D = __ldg(L.sh.bf_off + sd);
-        // an FP32 quartet leaves its final block in FP64 too (see contract_g32)
-        digest(L.ci, S + L.ci.out_base, 1, A, B, C, D, deg, L.P, L.K, L.ld, lane, 32);
-        __syncwarp();
-      }
-    }
+    Tally t;
+    for_each_range<BATCH>(L, gid, ng, lane, [&](const EriLaunch& Ls, long long q0, long long q1) {
+      g32_range<FOLD, MIXED>(Ls, q0, q1, S, CF, lane, t);
+    });
+    if (lane == 0) flush_tally(L, t);
   } else {
     for (long long t = gid; t < L.diag_n; t += ng) {
       const int p = __ldg(L.diag_list + t);
@@ -330,13 +364,6 @@ __global__ void __launch_bounds__(64, MIXED ? HFX_G32M_MINB : HFX_G32_MINB) eri_
     }
   }
   record_busy(L, t0);
-  if (L.counters && MODE == 0 && lane == 0) {
-    atomicAdd(L.counters + 0, n_prim);
-    atomicAdd(L.counters + 1, n_quart);
-    atomicAdd(L.counters + 2, n_skip);
-    atomicAdd(L.counters + 3, n32q);
-    atomicAdd(L.counters + 4, n32p);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -354,71 +381,68 @@ static int g32_stride(int cls) {
   return s + (s & 1) + 32 * NCOEF + 1;  // +1: stagger the groups' banks
 }
 
-size_t eri_smem_bytes(int cls, bool force32) {
-  if (!force32 && eri_group_size(cls) == 1) return sizeof(double) * (size_t)kClassInfo[cls].scratch * kBlock;
+// classes whose tables fold the accumulation (the thread-per-quartet ones)
+static bool class_folds(int cls) { return kClassInfo[cls].scratch <= HFX_G1_MAX_SCRATCH; }
+
+// The kernel instance for a class launch.  g32: warp groups (forced for mixed precision);
+// mode 1 = Schwarz diagonal; batch = quartets of several systems in one launch.
+static const void* kernel_ptr(int cls, int mode, bool g32, bool mixed, bool batch) {
+  const bool fold = class_folds(cls);
+  if (!g32) {
+    if (mode == 1) return (const void*)eri_g1_kernel<1, false>;
+    return batch ? (const void*)eri_g1_kernel<0, true> : (const void*)eri_g1_kernel<0, false>;
+  }
+  if (mode == 1) return fold ? (const void*)eri_g32_kernel<1, true, false, false> : (const void*)eri_g32_kernel<1, false, false, false>;
+  if (mixed) {
+    if (batch) return fold ? (const void*)eri_g32_kernel<0, true, true, true> : (const void*)eri_g32_kernel<0, false, true, true>;
+    return fold ? (const void*)eri_g32_kernel<0, true, true, false> : (const void*)eri_g32_kernel<0, false, true, false>;
+  }
+  if (batch) return fold ? (const void*)eri_g32_kernel<0, true, false, true> : (const void*)eri_g32_kernel<0, false, false, true>;
+  return fold ? (const void*)eri_g32_kernel<0, true, false, false> : (const void*)eri_g32_kernel<0, false, false, false>;
+}
+
+size_t eri_smem_bytes(int cls, bool g32) {
+  if (!g32) return sizeof(double) * (size_t)kClassInfo[cls].scratch * kBlock;
   return sizeof(double) * (size_t)g32_stride(cls) * (kBlock / 32);
 }
 
 int eri_block_size() { return kBlock; }
 
-// classes whose tables fold the accumulation (the thread-per-quartet ones)
-static bool class_folds(int cls) { return kClassInfo[cls].scratch <= HFX_G1_MAX_SCRATCH; }
-
-// force32 (mixed precision): warp groups for every class, with the FP32 path compiled in
-static const void* kernel_ptr(int cls, int mode, bool force32) {
-  const bool g1 = !force32 && eri_group_size(cls) == 1;
-  if (g1) return mode == 0 ? (const void*)eri_g1_kernel<0> : (const void*)eri_g1_kernel<1>;
-  const bool fold = class_folds(cls);
-  if (mode == 1) return fold ? (const void*)eri_g32_kernel<1, true, false> : (const void*)eri_g32_kernel<1, false, false>;
-  if (force32) return fold ? (const void*)eri_g32_kernel<0, true, true> : (const void*)eri_g32_kernel<0, false, true>;
-  return fold ? (const void*)eri_g32_kernel<0, true, false> : (const void*)eri_g32_kernel<0, false, false>;
-}
-
 cudaError_t eri_prepare() {
-  // allow the largest dynamic shared memory any class needs
+  // allow the largest dynamic shared memory any class needs, for every instance
   size_t mx = 0;
-  for (int c = 0; c < HFX_N_CLASSES; ++c) mx = std::max(mx, std::max(eri_smem_bytes(c, false), eri_smem_bytes(c, true)));
-  const void* ks[8] = {(const void*)eri_g1_kernel<0>, (const void*)eri_g1_kernel<1>,
-                       (const void*)eri_g32_kernel<0, false, false>, (const void*)eri_g32_kernel<1, false, false>,
-                       (const void*)eri_g32_kernel<0, true, false>, (const void*)eri_g32_kernel<1, true, false>,
-                       (const void*)eri_g32_kernel<0, false, true>, (const void*)eri_g32_kernel<0, true, true>};
-  for (auto k : ks) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-    if (e != cudaSuccess) return e;
+  for (int c = 0; c < HFX_N_CLASSES; ++c) {
+    mx = std::max(mx, eri_smem_bytes(c, true));
+    if (eri_group_size(c) == 1) mx = std::max(mx, eri_smem_bytes(c, false));  // only these run G = 1
   }
+  for (int cls : {0, HFX_N_CLASSES - 1})
+    for (int mode = 0; mode < 2; ++mode)
+      for (int g32 = 0; g32 < 2; ++g32)
+        for (int mixed = 0; mixed < 2; ++mixed)
+          for (int batch = 0; batch < 2; ++batch) {
+            cudaError_t e = cudaFuncSetAttribute(kernel_ptr(cls, mode, g32, mixed, batch),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+            if (e != cudaSuccess) return e;
+          }
   return cudaSuccess;
 }
 
-int eri_blocks_per_sm(int cls, int mode, bool force32) {
+int eri_blocks_per_sm(int cls, int mode, bool g32, bool mixed, bool batch) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(cls, mode, force32), kBlock,
-                                                    eri_smem_bytes(cls, force32)) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(cls, mode, g32, mixed, batch), kBlock,
+                                                    eri_smem_bytes(cls, g32)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
-cudaError_t eri_launch(const EriLaunch& L, int cls, int mode, int grid, cudaStream_t stream, bool force32) {
-  const size_t smem = eri_smem_bytes(cls, force32);
-  if (!force32 && eri_group_size(cls) == 1) {
-    if (mode == 0)
-      eri_g1_kernel<0><<<grid, kBlock, smem, stream>>>(L);
-    else
-      eri_g1_kernel<1><<<grid, kBlock, smem, stream>>>(L);
-  } else {
-    const int gs = g32_stride(cls);
-    const bool fold = class_folds(cls);
-    if (mode == 1) {
-      if (fold) eri_g32_kernel<1, true, false><<<grid, kBlock, smem, stream>>>(L, gs);
-      else eri_g32_kernel<1, false, false><<<grid, kBlock, smem, stream>>>(L, gs);
-    } else if (force32) {
-      if (fold) eri_g32_kernel<0, true, true><<<grid, kBlock, smem, stream>>>(L, gs);
-      else eri_g32_kernel<0, false, true><<<grid, kBlock, smem, stream>>>(L, gs);
-    } else {
-      if (fold) eri_g32_kernel<0, true, false><<<grid, kBlock, smem, stream>>>(L, gs);
-      else eri_g32_kernel<0, false, false><<<grid, kBlock, smem, stream>>>(L, gs);
-    }
-  }
-  return cudaGetLastError();
+cudaError_t eri_launch(const EriLaunch& L, int cls, int mode, int grid, cudaStream_t stream, bool g32, bool mixed,
+                       bool batch) {
+  const size_t smem = eri_smem_bytes(cls, g32);
+  const void* k = kernel_ptr(cls, mode, g32, mixed, batch);
+  int gs = g32_stride(cls);
+  void* args_g1[] = {(void*)&L};
+  void* args_g32[] = {(void*)&L, (void*)&gs};
+  return cudaLaunchKernel(k, dim3(grid), dim3(kBlock), g32 ? args_g32 : args_g1, smem, stream);
 }
 
 }  // namespace hfx

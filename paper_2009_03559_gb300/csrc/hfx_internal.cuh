@@ -171,6 +171,12 @@ struct EriLaunch {
   int fp32_ok;                  // mixed precision allowed for this class
   double fp32_tau;              // FP32 iff Q_IJ Q_KL max|P_blocks| < fp32_tau
   const double* Qs;             // Schwarz factor of each sorted pair
+  // batched launch (n_sys > 0): quartets of all systems' lists for this class, concatenated;
+  // seg[s] = first index of system s (seg[n_sys] = total = q_count); batch[s] = that
+  // system's record for this class (device memory)
+  int n_sys;
+  const long long* seg;
+  const EriLaunch* batch;
 };
 
 

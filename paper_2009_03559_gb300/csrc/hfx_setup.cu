@@ -323,6 +323,86 @@ __global__ void k_fma_chain(T* out, int iters, T a, T b) {
   if (s == (T)12345.678) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// ---------------------------------------------------------------------------
+// Batched forms: one launch for all systems of a batch (grid.y = system); every pointer
+// and size is read from the device table, so a captured graph is independent of them.
+// ---------------------------------------------------------------------------
+__global__ void k_batch_zero(const BatchSys* __restrict__ sys) {
+  const BatchSys b = sys[blockIdx.y];
+  const long long nn = (long long)b.n * b.n;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / b.n), j = (int)(t - (long long)i * b.n);
+    b.K[(size_t)i * b.ld + j] = 0.0;
+  }
+}
+
+__global__ void k_batch_pmax(const BatchSys* __restrict__ sys) {
+  const BatchSys b = sys[blockIdx.y];
+  const long long nn = (long long)b.ns * b.ns;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t / b.ns), J = (int)(t - (long long)I * b.ns);
+    const int oi = b.bf_off[I], oj = b.bf_off[J], ni = 2 * b.l[I] + 1, nj = 2 * b.l[J] + 1;
+    double m = 0.0;
+    for (int a = 0; a < ni; ++a)
+      for (int c = 0; c < nj; ++c) m = fmax(m, fabs(b.P[(size_t)(oi + a) * b.ld + oj + c]));
+    b.pmax[t] = m;
+  }
+}
+
+__global__ void k_batch_symmetrize(const BatchSys* __restrict__ sys) {
+  __shared__ double ta[32][33], tb[32][33];
+  const BatchSys b = sys[blockIdx.y];
+  const int nt = (b.n + 31) / 32;
+  const long long ntp = (long long)nt * (nt + 1) / 2;
+  for (long long t = blockIdx.x; t < ntp; t += gridDim.x) {
+    int bj = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((long long)bj * (bj + 1) / 2 > t) --bj;
+    while ((long long)(bj + 1) * (bj + 2) / 2 <= t) ++bj;
+    const int bi = (int)(t - (long long)bj * (bj + 1) / 2);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < 32; r += blockDim.y) {
+      const int i = bi * 32 + r, j = bj * 32 + tx;
+      ta[r][tx] = (i < b.n && j < b.n) ? b.K[(size_t)i * b.ld + j] : 0.0;
+      const int i2 = bj * 32 + r, j2 = bi * 32 + tx;
+      tb[r][tx] = (i2 < b.n && j2 < b.n) ? b.K[(size_t)i2 * b.ld + j2] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += blockDim.y) {
+      const int i = bi * 32 + r, j = bj * 32 + tx;
+      if (i < b.n && j < b.n) b.K[(size_t)i * b.ld + j] = ta[r][tx] + tb[tx][r];
+      const int i2 = bj * 32 + r, j2 = bi * 32 + tx;
+      if (bi != bj && i2 < b.n && j2 < b.n) b.K[(size_t)i2 * b.ld + j2] = tb[r][tx] + ta[tx][r];
+    }
+    __syncthreads();
+  }
+}
+
+// one block per system: compensated sum of P K
+__global__ void k_batch_trace(const BatchSys* __restrict__ sys) {
+  const BatchSys b = sys[blockIdx.x];
+  __shared__ double ss[256], cc[256];
+  double s = 0.0, c = 0.0;
+  const long long nn = (long long)b.n * b.n;
+  for (long long t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int i = (int)(t / b.n), j = (int)(t - (long long)i * b.n);
+    double e;
+    two_sum(s, b.P[(size_t)i * b.ld + j] * b.K[(size_t)i * b.ld + j], s, e);
+    c += e;
+  }
+  ss[threadIdx.x] = s;
+  cc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double e;
+      two_sum(ss[threadIdx.x], ss[threadIdx.x + w], ss[threadIdx.x], e);
+      cc[threadIdx.x] += cc[threadIdx.x + w] + e;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) b.energy[0] = ss[0] + cc[0];
+}
+
 // ===========================================================================
 // Host wrappers
 // ===========================================================================
@@ -445,6 +525,20 @@ cudaError_t launch_pmax(int ns, const int* bf_off, const int* l, const double* P
   const long long n = (long long)ns * ns;
   if (n <= 0) return cudaSuccess;
   k_pmax<<<nblk(n, 256), 256, 0, s>>>(ns, bf_off, l, P, ld, pmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_prologue(const BatchSys* sys, int n, int n_sm, bool pmax, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_batch_zero<<<dim3(2 * n_sm, n), 256, 0, s>>>(sys);
+  if (pmax) k_batch_pmax<<<dim3(n_sm, n), 256, 0, s>>>(sys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_epilogue(const BatchSys* sys, int n, int n_sm, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_batch_symmetrize<<<dim3(n_sm, n), dim3(32, 8), 0, s>>>(sys);
+  k_batch_trace<<<n, 256, 0, s>>>(sys);
   return cudaGetLastError();
 }
 

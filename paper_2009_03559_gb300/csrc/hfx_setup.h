@@ -5,6 +5,17 @@
 
 namespace hfx {
 
+// One system of a batched K build (device table; read by the batched kernels).
+struct BatchSys {
+  const double* P;
+  double* K;
+  int n, ld, ns;
+  const int* bf_off;
+  const int* l;
+  double* pmax;
+  double* energy;
+};
+
 // Rows of the quartet task list: class pair cp = hi(hi+1)/2 + lo owns rows
 // [row_base[cp], row_base[cp+1]), one per bra pair of bin hi.
 struct RowTable {
@@ -46,6 +57,8 @@ cudaError_t launch_finalize(int n, int ld, const double* P, double* K, double* p
                             cudaStream_t s);
 cudaError_t launch_pmax(int ns, const int* bf_off, const int* l, const double* P, int ld, double* pmax,
                         cudaStream_t s);
+cudaError_t launch_batch_prologue(const BatchSys* sys, int n, int n_sm, bool pmax, cudaStream_t s);
+cudaError_t launch_batch_epilogue(const BatchSys* sys, int n, int n_sm, cudaStream_t s);
 cudaError_t fma_peak(double* fp64_tflops, double* fp32_tflops);
 
 }  // namespace hfx

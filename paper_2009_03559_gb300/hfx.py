@@ -57,6 +57,18 @@ class Stats(ctypes.Structure):
         }
 
 
+class BatchStats(ctypes.Structure):
+    _fields_ = [("n_quartets", ctypes.c_int64), ("ms_last", ctypes.c_double),
+                ("group_size_class", ctypes.c_int32 * 21), ("chunk_class", ctypes.c_int32 * 21),
+                ("tune_ms_class", ctypes.c_double * 21)]
+
+    def as_dict(self):
+        return {"n_quartets": int(self.n_quartets), "ms_last": float(self.ms_last),
+                "group_size_class": [int(x) for x in self.group_size_class],
+                "chunk_class": [int(x) for x in self.chunk_class],
+                "tune_ms_class": [float(x) for x in self.tune_ms_class]}
+
+
 _lib = None
 
 
@@ -98,6 +110,21 @@ def load_library(path: str = LIB_PATH):
     L.hfx_last_error.restype = ctypes.c_char_p
     L.hfx_free.argtypes = [vp]
     L.hfx_free.restype = None
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    L.hfx_batch_create.argtypes = [ctypes.POINTER(vp), pp, ctypes.c_int, vp]
+    L.hfx_batch_create.restype = ctypes.c_int
+    L.hfx_batch_tune.argtypes = [vp, pp, pp, ip]
+    L.hfx_batch_tune.restype = ctypes.c_int
+    L.hfx_batch_run.argtypes = [vp, pp, pp, ip]
+    L.hfx_batch_run.restype = ctypes.c_int
+    L.hfx_batch_set_graph.argtypes = [vp, ctypes.c_int]
+    L.hfx_batch_set_graph.restype = ctypes.c_int
+    L.hfx_batch_get_stats.argtypes = [vp, ctypes.POINTER(BatchStats)]
+    L.hfx_batch_get_stats.restype = ctypes.c_int
+    L.hfx_batch_free.argtypes = [vp]
+    L.hfx_batch_free.restype = None
+    L.hfx_build_K_batched.argtypes = [pp, pp, pp, ip, ctypes.c_int]
+    L.hfx_build_K_batched.restype = ctypes.c_int
     L.hfx_energy_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
     L.hfx_energy_noalloc.restype = ctypes.c_int
     L.hfx_measure_fma_peak.argtypes = [dp, dp]
@@ -243,6 +270,64 @@ class HFX:
     def close(self):
         if getattr(self, "h", None):
             self.L.hfx_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr_array(values):
+    arr = (ctypes.c_void_p * len(values))(*[ctypes.c_void_p(int(v)) for v in values])
+    return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
+
+
+class Batch:
+    """Batched K builds over several ``HFX`` contexts (one launch per angular class for all
+    systems, captured once as a CUDA graph and replayed)."""
+
+    def __init__(self, contexts, stream=None, graph=True):
+        self.L = load_library()
+        self.contexts = list(contexts)
+        ptrs, self._keep = _ptr_array([c.h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        rc = self.L.hfx_batch_create(ctypes.byref(h), ptrs, len(self.contexts), st)
+        if rc != 0:
+            raise HFXError(rc, self.L.hfx_last_error(None).decode())
+        self.h = h
+        if not graph:
+            self.L.hfx_batch_set_graph(h, 0)
+
+    def _args(self, Ps, Ks):
+        pP, kP = _ptr_array([P.data_ptr() for P in Ps])
+        pK, kK = _ptr_array([K.data_ptr() for K in Ks])
+        ld = (ctypes.c_int * len(Ps))(*[int(P.stride(0)) for P in Ps])
+        return pP, pK, ctypes.cast(ld, ctypes.POINTER(ctypes.c_int)), (kP, kK, ld)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise HFXError(rc, self.L.hfx_last_error(None).decode())
+
+    def tune(self, Ps, Ks):
+        pP, pK, ld, keep = self._args(Ps, Ks)
+        self._check(self.L.hfx_batch_tune(self.h, pP, pK, ld))
+
+    def run(self, Ps, Ks):
+        pP, pK, ld, keep = self._args(Ps, Ks)
+        self._keep_run = keep
+        self._check(self.L.hfx_batch_run(self.h, pP, pK, ld))
+
+    def stats(self):
+        s = BatchStats()
+        self._check(self.L.hfx_batch_get_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.hfx_batch_free(self.h)
             self.h = None
 
     def __del__(self):
