@@ -49,7 +49,8 @@ extern "C" {
 #define HFX_ERR_OOM -3            /* device allocation failed */
 #define HFX_ERR_CUDA -4           /* a CUDA call or kernel launch failed */
 #define HFX_ERR_STATE -5          /* call order violated (e.g. build_K before build_pairs) */
-#define HFX_ERR_TIMEOUT -6        /* a bounded device wait gave up */
+#define HFX_ERR_TIMEOUT -6        /* a bounded wait gave up */
+#define HFX_ERR_ADMISSION -7      /* a request can never fit the server's memory budget */
 
 /* precision modes */
 #define HFX_FP64 0                /* every integral in FP64 */
@@ -68,9 +69,10 @@ typedef struct {
   double schwarz_tau;  /* Schwarz threshold tau (>= 0) */
   double rcut_bohr;    /* orbital cutoff radius r_c; <= 0 disables the pair-distance screen */
   double prim_tau;     /* primitive pairs with |prefactor| below this are dropped (default 1e-22) */
-  double fp32_tau;     /* HFX_MIXED: a quartet's recurrences (VRR, HRR, spherical step) run in FP32
-                          iff Q_IJ Q_KL max(|P_bd|,|P_bc|,|P_ad|,|P_ac|) < fp32_tau (default 1e-6);
-                          the Boys step and all K accumulation stay FP64 */
+  double fp32_tau;     /* HFX_MIXED: a quartet's primitive recurrences (VRR) and their contraction
+                          run in FP32 iff Q_IJ Q_KL Pmax < fp32_tau (default 1e-6), Pmax as set
+                          by fp32_pmax_global; the Boys step, HRR, spherical step and all K
+                          accumulation stay FP64 */
   int precision;       /* HFX_FP64 (default) or HFX_MIXED */
   int schedule;        /* HFX_SCHED_DYNAMIC (default), HFX_SCHED_QUARTET or HFX_SCHED_PAIR */
   int skip_zero_p;     /* 1 (default): skip quartets whose four density blocks P_bd, P_bc,
@@ -78,7 +80,10 @@ typedef struct {
   int fp32_class_mask; /* HFX_MIXED: bit c allows FP32 for quartet class c (index as in
                           n_quartets_class); default 0x3F = the six classes without d shells
                           (recurrences of d classes stay FP64) */
-  int reserved[4];     /* set to 0 */
+  int fp32_pmax_global;/* HFX_MIXED: 0 (default): Pmax = max(|P_bd|,|P_bc|,|P_ad|,|P_ac|), the
+                          largest density element the quartet's four K updates multiply;
+                          1: Pmax = max |P| over the whole matrix (more conservative) */
+  int reserved[3];     /* set to 0 */
 } hfx_options;
 
 typedef struct {
@@ -156,6 +161,10 @@ int hfx_set_timing(hfx_ctx* ctx, int enable);
 /* Number of basis functions of the context, or a negative error code. */
 int hfx_n_basis(const hfx_ctx* ctx);
 
+/* Device bytes the context holds (basis, pair list, per-build scratch), or a negative
+ * error code. */
+int64_t hfx_device_bytes(const hfx_ctx* ctx);
+
 /* Copies the kept pairs (shell a, shell b with l_a >= l_b, Q) in bin order to host
  * arrays of length >= max_n; returns the number of kept pairs or an error code. */
 int64_t hfx_get_pairs(hfx_ctx* ctx, int* shell_a, int* shell_b, double* q, int64_t max_n);
@@ -187,7 +196,8 @@ typedef struct {
   double ms_last;              /* GPU time of the last hfx_batch_run (events around it) */
   int32_t group_size_class[21];/* chosen lanes per quartet (1 or 32) per class */
   int32_t chunk_class[21];     /* chosen quartets per dynamic claim per class */
-  double tune_ms_class[21];    /* best class-launch time seen by the tuner */
+  double tune_ms_class[21];    /* best tuning time per class, scaled from its window to the class */
+  int64_t tune_window_class[21]; /* quartets in the window each candidate was timed on */
 } hfx_batch_stats;
 
 /* Creates a batch over n contexts (all with pair lists, same device).  Runs are ordered
@@ -207,6 +217,10 @@ int hfx_batch_tune(hfx_batch* b, const double* const* P_dev, double* const* K_de
  * Asynchronous; E_K of system s lands in its context (hfx_energy). */
 int hfx_batch_run(hfx_batch* b, const double* const* P_dev, double* const* K_dev, const int* ld);
 
+/* Launch time the tuner aims at per candidate (default 20 ms): each class's candidates are
+ * timed on one window of its quartet list, grown from 16k quartets to about this time. */
+int hfx_batch_set_tune_target(hfx_batch* b, double ms);
+
 /* 1 (default): capture and replay a CUDA graph; 0: plain launches every run. */
 int hfx_batch_set_graph(hfx_batch* b, int enable);
 
@@ -215,6 +229,106 @@ void hfx_batch_free(hfx_batch* b);
 
 /* One-shot form: create a batch, run it once, free it. */
 int hfx_build_K_batched(hfx_ctx* const* ctxs, const double* const* P_dev, double* const* K_dev, const int* ld, int n);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop over registered systems with continuous batching.
+ *
+ * Systems (contexts with pair lists) are registered once and stay resident: basis,
+ * pair lists and Boys table live on the device for the server's life.  A request names
+ * a system and gives a density P and a destination for K.  The server keeps a FIFO
+ * queue and up to max_inflight steps on the device at once, each on a stream of its
+ * own.  Whenever a step slot is free, all queued requests that fit (at most max_batch,
+ * in arrival order, while the memory budget allows) form one step: their P are copied
+ * to server-owned device buffers, one batched launch per class evaluates all their
+ * quartets (as hfx_batch_run), and each K goes to its destination.  Requests arriving
+ * while steps run are admitted as soon as a slot and memory free up, so their work
+ * overlaps on the device with the steps still running.
+ *
+ * Admission by memory: the server holds the resident systems, its step workspaces and,
+ * for every admitted request, P, K and the density-block maxima (2 n_bf^2 + n_shells^2
+ * doubles).  A queued request is admitted only while the total stays within
+ * hbm_budget_gb; a request that could never fit is refused with HFX_ERR_ADMISSION.
+ *
+ * The server is single-threaded and driven by its callers: every submit, poll, wait and
+ * progress call retires finished steps and starts new ones.  Calls are serialised by an
+ * internal lock, so several host threads may share one server.
+ * ------------------------------------------------------------------------- */
+typedef struct hfx_server hfx_server;
+
+typedef struct {
+  double hbm_budget_gb;  /* device memory the server may hold (default 120 GB) */
+  int max_inflight;      /* steps on the device at once, each on its own stream (default 4) */
+  int max_batch;         /* most requests in one step (default 16) */
+  int precision;         /* HFX_FP64 (default) or HFX_MIXED for every request; the FP32 test
+                            uses each system's fp32_tau, fp32_class_mask and fp32_pmax_global */
+  int reserved[5];       /* set to 0 */
+} hfx_server_options;
+
+#define HFX_REQ_DONE 0
+#define HFX_REQ_QUEUED 1
+#define HFX_REQ_RUNNING 2
+
+typedef struct {
+  uint64_t ticket;
+  int32_t status;        /* HFX_REQ_DONE, _QUEUED, _RUNNING or a negative HFX_ERR_* code */
+  int32_t system_id;
+  int32_t step_size;     /* requests in the step that computed it */
+  int32_t pad;
+  double energy;         /* E_K = sum P K of this request */
+  double t_submit_ms;    /* times since server creation: submit call, */
+  double t_admit_ms;     /* step launch (host clock), */
+  double t_done_ms;      /* end of the step's work on the device (CUDA events) */
+  double ms_step;        /* device time of the step, P copy-in to K copy-out */
+  int64_t n_quartets;    /* screened quartets of the system */
+} hfx_result;
+
+typedef struct {
+  int64_t n_submitted, n_done, n_failed, n_steps, n_queued, n_running;
+  int64_t quartets_done;
+  int64_t bytes_resident;  /* registered systems + step workspaces */
+  int64_t bytes_requests;  /* admitted requests now */
+  int64_t bytes_peak;      /* largest resident + requests seen */
+  int32_t max_step_size, max_steps_inflight;
+} hfx_server_stats;
+
+void hfx_server_default_options(hfx_server_options* opt);
+
+/* Creates a server on the current device.  opt may be NULL for defaults. */
+int hfx_server_create(hfx_server** out, const hfx_server_options* opt);
+
+/* Registers a context (with its pair list) as system *id.  The server neither copies nor
+ * frees it: the context must outlive the server and must not be rebuilt meanwhile.  Its
+ * device bytes count against the budget (HFX_ERR_ADMISSION if they do not fit).
+ * Synchronises the context's stream. */
+int hfx_server_add_system(hfx_server* srv, hfx_ctx* ctx, int* id);
+
+/* Queues K = K(P) for system `id`.  P (n_bf x n_bf, row-major, ld = n_bf) and K_out (same
+ * shape) are device pointers or page-locked host pointers (pageable host memory is refused
+ * with HFX_ERR_ARG, because copies to and from it would block the server).  P must stay
+ * valid until the request is admitted and K_out until it is done.  The server waits for
+ * the work queued on `stream` (the stream that produced P; NULL = legacy default stream)
+ * before it reads P.  *ticket identifies the request.  Errors: HFX_ERR_ARG,
+ * HFX_ERR_ADMISSION. */
+int hfx_serve_submit(hfx_server* srv, int id, const double* P, double* K_out, void* stream, uint64_t* ticket);
+
+/* Drives the server and reports the request's state in *out without waiting. */
+int hfx_serve_poll(hfx_server* srv, uint64_t ticket, hfx_result* out);
+
+/* Drives the server until the request is done or failed, or timeout_ms (< 0: no limit)
+ * passes (then HFX_ERR_TIMEOUT, with the request still queued or running). */
+int hfx_serve_wait(hfx_server* srv, uint64_t ticket, double timeout_ms, hfx_result* out);
+
+/* Retires finished steps and starts new ones; returns the number of requests not done. */
+int hfx_serve_progress(hfx_server* srv);
+
+/* Drives the server until every request is done (HFX_ERR_TIMEOUT after timeout_ms >= 0). */
+int hfx_serve_drain(hfx_server* srv, double timeout_ms);
+
+int hfx_server_get_stats(hfx_server* srv, hfx_server_stats* out);
+const char* hfx_server_last_error(const hfx_server* srv);
+
+/* Waits for every step, then frees the server's own memory (not the contexts). */
+void hfx_server_free(hfx_server* srv);
 
 /* Largest matrix order accepted by hfx_energy_noalloc (rows of its fixed scratch). */
 #define HFX_NOALLOC_MAX_N 16384

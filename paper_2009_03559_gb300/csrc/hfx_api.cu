@@ -10,72 +10,9 @@
 #include "hfx_eri.h"
 #include "hfx_internal.cuh"
 #include "hfx_setup.h"
+#include "hfx_ctx.h"
 
 using namespace hfx;
-
-// device counters per class: primitive quartets evaluated, quartets evaluated, primitive
-// quartets dropped at the Boys step, quartets in FP32, primitive quartets in FP32
-static const int kNCnt = 5;
-
-struct hfx_ctx {
-  cudaStream_t stream = nullptr;
-  hfx_options opt{};
-  std::string err;
-  int n_atoms = 0, n_shells = 0, n_bf = 0, n_prim = 0, n_sm = 0;
-  std::vector<int> h_l;
-  // basis (device)
-  double *d_xyz = nullptr, *d_alpha = nullptr, *d_coef = nullptr, *d_w = nullptr, *d_boys = nullptr;
-  int *d_atom = nullptr, *d_l = nullptr, *d_nprim = nullptr, *d_prim_off = nullptr, *d_bf_off = nullptr;
-  // pairs (device)
-  int n_cand = 0, n_kept = 0;
-  int *d_sa = nullptr, *d_sb = nullptr, *d_pcls = nullptr, *d_pp_off = nullptr, *d_pp_n = nullptr;
-  double *d_AB = nullptr, *d_Q = nullptr, *d_Qs = nullptr;
-  PrimPair* d_pp = nullptr;
-  int* d_sorted = nullptr;
-  RowTable rt{};
-  int n_rows = 0;
-  long long* d_qoff = nullptr;
-  long long cls_q[21] = {}, cls_qbegin[21] = {};
-  bool pairs_ready = false;
-  // per build
-  double *d_energy = nullptr, *d_part = nullptr, *d_pmax = nullptr;
-  int n_part = 0;
-  double *d_Pst = nullptr, *d_Kst = nullptr;
-  unsigned long long* d_busy = nullptr;      // per SM
-  unsigned long long* d_counters = nullptr;  // kNCnt per class
-  unsigned long long* d_work = nullptr;      // dynamic-schedule claim counter per class
-  bool timing = false;
-  cudaEvent_t ev[2 * 21 + 4] = {};
-  bool ev_ok = false;
-  bool class_launched[21] = {};
-  hfx_stats stats{};
-  float ms_pairs = 0.f;
-  std::vector<void*> allocs;       // owned for the context lifetime
-  std::vector<void*> pair_allocs;  // owned until the next build_pairs
-
-  int fail(int code, const std::string& msg) {
-    err = msg;
-    return code;
-  }
-  int cuda_fail(const char* what, cudaError_t e) {
-    err = std::string(what) + ": " + cudaGetErrorString(e);
-    return e == cudaErrorMemoryAllocation ? HFX_ERR_OOM : HFX_ERR_CUDA;
-  }
-  template <class T>
-  int alloc(T** p, size_t n, bool pair_scope = false) {
-    *p = nullptr;
-    if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
-    if (e != cudaSuccess) return cuda_fail("cudaMalloc", e);
-    (pair_scope ? pair_allocs : allocs).push_back(*p);
-    return HFX_OK;
-  }
-  void free_pairs() {
-    for (void* p : pair_allocs) cudaFree(p);
-    pair_allocs.clear();
-    pairs_ready = false;
-  }
-};
 
 static thread_local std::string g_init_err;
 
@@ -129,6 +66,7 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
   if (opt) o = *opt;
   if (!(o.omega >= 0.0) || !(o.schwarz_tau >= 0.0) || !(o.prim_tau >= 0.0) || !(o.fp32_tau >= 0.0) ||
       (o.precision != HFX_FP64 && o.precision != HFX_MIXED) ||
+      (o.fp32_pmax_global != 0 && o.fp32_pmax_global != 1) ||
       (o.schedule != HFX_SCHED_QUARTET && o.schedule != HFX_SCHED_PAIR && o.schedule != HFX_SCHED_DYNAMIC)) {
     g_init_err = "invalid options";
     return HFX_ERR_ARG;
@@ -188,7 +126,8 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
       (r = ctx->alloc(&ctx->d_prim_off, n_shells)) || (r = ctx->alloc(&ctx->d_bf_off, n_shells)) ||
       (r = ctx->alloc(&ctx->d_energy, 1)) || (r = ctx->alloc(&ctx->d_busy, 1024)) ||
       (r = ctx->alloc(&ctx->d_counters, kNCnt * 21)) ||
-      (r = ctx->alloc(&ctx->d_pmax, (size_t)n_shells * n_shells)) || (r = ctx->alloc(&ctx->d_work, 32)))
+      (r = ctx->alloc(&ctx->d_pmax, (size_t)n_shells * n_shells)) || (r = ctx->alloc(&ctx->d_work, 32)) ||
+      (r = ctx->alloc(&ctx->d_pglob, 1)))
     return bail(r);
   ctx->n_part = 2 * ctx->n_sm;
   if ((r = ctx->alloc(&ctx->d_part, 2 * (size_t)ctx->n_part))) return bail(r);
@@ -235,7 +174,7 @@ static double setup_flops(int E, int F, int Lt, bool erfc) {
 // a primitive quartet dropped at kappa T >= table end costs the set-up up to that test
 static double skip_flops() { return 1 + 4 + 3 + 9 + 6 + 2 + 7; }
 
-static EriLaunch base_launch(hfx_ctx* ctx) {
+EriLaunch hfx::base_launch(hfx_ctx* ctx) {
   EriLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.pa.sa = ctx->d_sa;
@@ -452,8 +391,10 @@ extern "C" int hfx_build_K(hfx_ctx* ctx, const double* P, double* K, int ld) {
   if (ctx->opt.schedule == HFX_SCHED_DYNAMIC) CK(cudaMemsetAsync(ctx->d_work, 0, 32 * sizeof(unsigned long long), s));
   const bool mixed = ctx->opt.precision == HFX_MIXED;
   if (ctx->opt.skip_zero_p || mixed) {
-    CK(launch_pmax(ctx->n_shells, ctx->d_bf_off, ctx->d_l, P, ld, ctx->d_pmax, s));
+    const bool glob = mixed && ctx->opt.fp32_pmax_global;
+    CK(launch_pmax(ctx->n_shells, ctx->d_bf_off, ctx->d_l, P, ld, ctx->d_pmax, glob ? ctx->d_pglob : nullptr, s));
     L.pmax = ctx->d_pmax;
+    L.pglob = glob ? ctx->d_pglob : nullptr;
     L.ns = ctx->n_shells;
   }
   L.skip_zero = ctx->opt.skip_zero_p;
@@ -561,6 +502,10 @@ extern "C" int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out) {
 
 extern "C" int hfx_n_basis(const hfx_ctx* ctx) { return ctx ? ctx->n_bf : HFX_ERR_ARG; }
 
+extern "C" int64_t hfx_device_bytes(const hfx_ctx* ctx) {
+  return ctx ? (int64_t)(ctx->bytes + ctx->pair_bytes) : HFX_ERR_ARG;
+}
+
 extern "C" int64_t hfx_get_pairs(hfx_ctx* ctx, int* shell_a, int* shell_b, double* q, int64_t max_n) {
   if (!ctx) return HFX_ERR_ARG;
   if (!ctx->pairs_ready) return ctx->fail(HFX_ERR_STATE, "no pair list");
@@ -616,342 +561,3 @@ extern "C" int hfx_measure_fma_peak(double* fp64_tflops, double* fp32_tflops) {
   return HFX_OK;
 }
 
-// ===========================================================================
-// Batched K builds
-// ===========================================================================
-struct hfx_batch {
-  std::vector<hfx_ctx*> ctx;
-  cudaStream_t user = nullptr;    // the caller's stream (may be the legacy default stream)
-  cudaStream_t stream = nullptr;  // the batch's own stream: graphs are captured and run here
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  int n = 0, n_sm = 0;
-  bool mixed = false, skip_zero = true, use_graph = true;
-  long long total[21] = {};
-  int g32[21] = {}, chunk[21] = {};
-  double tune_ms[21] = {};
-  // device tables and their pinned host mirrors (launch records [class][system], systems)
-  EriLaunch* d_launch = nullptr;
-  EriLaunch* h_launch = nullptr;
-  BatchSys* d_sys = nullptr;
-  BatchSys* h_sys = nullptr;
-  long long* d_seg = nullptr;
-  unsigned long long* d_work = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  bool ran = false;
-  float ms_last = 0.f;
-  std::string err;
-  int fail(int code, const std::string& m) {
-    err = m;
-    hfx::set_global_error(m);
-    return code;
-  }
-};
-
-#define CKB(call)                                                                     \
-  do {                                                                                \
-    cudaError_t e_ = (call);                                                          \
-    if (e_ != cudaSuccess) return b->fail(HFX_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
-  } while (0)
-
-extern "C" void hfx_batch_free(hfx_batch* b) {
-  if (!b) return;
-  if (b->stream) cudaStreamSynchronize(b->stream);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  cudaFree(b->d_launch);
-  cudaFree(b->d_sys);
-  cudaFree(b->d_seg);
-  cudaFree(b->d_work);
-  cudaFreeHost(b->h_launch);
-  cudaFreeHost(b->h_sys);
-  if (b->e0) cudaEventDestroy(b->e0);
-  if (b->e1) cudaEventDestroy(b->e1);
-  if (b->ev_in) cudaEventDestroy(b->ev_in);
-  if (b->ev_out) cudaEventDestroy(b->ev_out);
-  if (b->stream) cudaStreamDestroy(b->stream);
-  delete b;
-}
-
-extern "C" int hfx_batch_create(hfx_batch** out, hfx_ctx* const* ctxs, int n, void* stream) {
-  if (!out || !ctxs || n <= 0) {
-    hfx::set_global_error("hfx_batch_create: NULL argument or n <= 0");
-    return HFX_ERR_ARG;
-  }
-  *out = nullptr;
-  for (int s = 0; s < n; ++s)
-    if (!ctxs[s] || !ctxs[s]->pairs_ready) {
-      hfx::set_global_error("hfx_batch_create: context " + std::to_string(s) + " has no pair list");
-      return HFX_ERR_STATE;
-    }
-  hfx_batch* b = new hfx_batch();
-  b->ctx.assign(ctxs, ctxs + n);
-  b->n = n;
-  b->user = stream ? (cudaStream_t)stream : ctxs[0]->stream;
-  b->n_sm = ctxs[0]->n_sm;
-  b->mixed = ctxs[0]->opt.precision == HFX_MIXED;
-  b->skip_zero = ctxs[0]->opt.skip_zero_p != 0;
-  auto bail = [&](int code) {
-    hfx_batch_free(b);
-    return code;
-  };
-  std::vector<long long> seg(21 * (size_t)(n + 1));
-  for (int cp = 0; cp < 21; ++cp) {
-    long long acc = 0;
-    for (int s = 0; s < n; ++s) {
-      seg[cp * (n + 1) + s] = acc;
-      acc += ctxs[s]->cls_q[cp];
-    }
-    seg[cp * (n + 1) + n] = acc;
-    b->total[cp] = acc;
-    b->g32[cp] = (b->mixed || eri_group_size(cp) == 32) ? 1 : 0;
-    b->chunk[cp] = b->g32[cp] ? 8 : 256;
-  }
-  cudaError_t e;
-  if ((e = cudaMalloc(&b->d_launch, sizeof(EriLaunch) * 21 * n)) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_sys, sizeof(BatchSys) * n)) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_seg, sizeof(long long) * seg.size())) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_work, sizeof(unsigned long long) * 32)) != cudaSuccess ||
-      (e = cudaMallocHost(&b->h_launch, sizeof(EriLaunch) * 21 * n)) != cudaSuccess ||
-      (e = cudaMallocHost(&b->h_sys, sizeof(BatchSys) * n)) != cudaSuccess ||
-      (e = cudaEventCreate(&b->e0)) != cudaSuccess || (e = cudaEventCreate(&b->e1)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) {
-    hfx::set_global_error(std::string("hfx_batch_create: ") + cudaGetErrorString(e));
-    return bail(e == cudaErrorMemoryAllocation ? HFX_ERR_OOM : HFX_ERR_CUDA);
-  }
-  e = cudaMemcpy(b->d_seg, seg.data(), sizeof(long long) * seg.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    hfx::set_global_error(std::string("hfx_batch_create: ") + cudaGetErrorString(e));
-    return bail(HFX_ERR_CUDA);
-  }
-  // per-system launch records of every class (P, K, ld filled in per run)
-  for (int s = 0; s < n; ++s) {
-    hfx_ctx* c = ctxs[s];
-    for (int cp = 0; cp < 21; ++cp) {
-      int hi = 0;
-      while ((hi + 1) * (hi + 2) / 2 <= cp) ++hi;
-      const int lo = cp - hi * (hi + 1) / 2;
-      EriLaunch L = base_launch(c);
-      L.ci = class_info_host()[cp];
-      L.sorted = c->d_sorted;
-      L.qoff = c->d_qoff;
-      L.row_begin = c->rt.row_base[cp];
-      L.row_end = c->rt.row_base[cp + 1];
-      L.bra_bin_start = c->rt.bin_start[hi];
-      L.ket_bin_start = c->rt.bin_start[lo];
-      L.q_begin = c->cls_qbegin[cp];
-      L.q_count = c->cls_q[cp];
-      L.pmax = (b->skip_zero || b->mixed) ? c->d_pmax : nullptr;
-      L.ns = c->n_shells;
-      L.skip_zero = b->skip_zero;
-      L.fp32_ok = b->mixed && ((c->opt.fp32_class_mask >> cp) & 1);
-      L.fp32_tau = c->opt.fp32_tau;
-      L.Qs = c->d_Qs;
-      b->h_launch[cp * n + s] = L;
-    }
-    BatchSys& y = b->h_sys[s];
-    y.P = nullptr;
-    y.K = nullptr;
-    y.n = c->n_bf;
-    y.ld = c->n_bf;
-    y.ns = c->n_shells;
-    y.bf_off = c->d_bf_off;
-    y.l = c->d_l;
-    y.pmax = c->d_pmax;
-    y.energy = c->d_energy;
-  }
-  *out = b;
-  return HFX_OK;
-}
-
-// refresh the P/K/ld fields of the host mirrors; true if anything changed
-static bool batch_set_buffers(hfx_batch* b, const double* const* P, double* const* K, const int* ld) {
-  bool changed = false;
-  for (int s = 0; s < b->n; ++s) {
-    const int l = ld ? ld[s] : b->ctx[s]->n_bf;
-    BatchSys& y = b->h_sys[s];
-    if (y.P != P[s] || y.K != K[s] || y.ld != l) changed = true;
-    y.P = P[s];
-    y.K = K[s];
-    y.ld = l;
-    for (int cp = 0; cp < 21; ++cp) {
-      EriLaunch& L = b->h_launch[cp * b->n + s];
-      L.P = P[s];
-      L.K = K[s];
-      L.ld = l;
-    }
-  }
-  return changed;
-}
-
-static EriLaunch batch_class_launch(hfx_batch* b, int cp) {
-  EriLaunch L;
-  std::memset(&L, 0, sizeof(L));
-  L.ci = class_info_host()[cp];
-  L.schedule = HFX_SCHED_DYNAMIC;
-  L.q_count = b->total[cp];
-  L.work = b->d_work + cp;
-  L.chunk = b->chunk[cp];
-  L.n_sys = b->n;
-  L.seg = b->d_seg + (size_t)cp * (b->n + 1);
-  L.batch = b->d_launch + (size_t)cp * b->n;
-  return L;
-}
-
-static int batch_grid(hfx_batch* b, int cp) {
-  const int gs = b->g32[cp] ? 32 : 1;
-  const long long groups_per_block = eri_block_size() / gs;
-  const long long need = (b->total[cp] + groups_per_block - 1) / groups_per_block;
-  const long long cap =
-      (long long)eri_blocks_per_sm(cp, 0, b->g32[cp], b->mixed && b->g32[cp], true) * b->n_sm;
-  return (int)std::max(1LL, std::min(need, cap));
-}
-
-// the whole batched build on the stream
-static int batch_enqueue(hfx_batch* b) {
-  cudaStream_t s = b->stream;
-  CKB(cudaMemcpyAsync(b->d_launch, b->h_launch, sizeof(EriLaunch) * 21 * b->n, cudaMemcpyHostToDevice, s));
-  CKB(cudaMemcpyAsync(b->d_sys, b->h_sys, sizeof(BatchSys) * b->n, cudaMemcpyHostToDevice, s));
-  CKB(cudaMemsetAsync(b->d_work, 0, 32 * sizeof(unsigned long long), s));
-  CKB(launch_batch_prologue(b->d_sys, b->n, b->n_sm, b->skip_zero || b->mixed, s));
-  for (int cp = 0; cp < 21; ++cp) {
-    if (b->total[cp] == 0) continue;
-    const EriLaunch L = batch_class_launch(b, cp);
-    CKB(eri_launch(L, cp, 0, batch_grid(b, cp), s, b->g32[cp], b->mixed && b->g32[cp], true));
-  }
-  CKB(launch_batch_epilogue(b->d_sys, b->n, b->n_sm, s));
-  return HFX_OK;
-}
-
-extern "C" int hfx_batch_set_graph(hfx_batch* b, int enable) {
-  if (!b) return HFX_ERR_ARG;
-  b->use_graph = enable != 0;
-  return HFX_OK;
-}
-
-extern "C" int hfx_batch_run(hfx_batch* b, const double* const* P, double* const* K, const int* ld) {
-  if (!b || !P || !K) return HFX_ERR_ARG;
-  for (int s = 0; s < b->n; ++s)
-    if (!P[s] || !K[s] || (ld && ld[s] < b->ctx[s]->n_bf))
-      return b->fail(HFX_ERR_ARG, "hfx_batch_run: NULL matrix or ld < n_bf for system " + std::to_string(s));
-  // the mirrors may still be read by a previous run's copies: wait before rewriting
-  if (b->ran) CKB(cudaStreamSynchronize(b->stream));
-  batch_set_buffers(b, P, K, ld);
-  cudaStream_t s = b->stream;
-  CKB(cudaEventRecord(b->ev_in, b->user));  // the inputs are ready on the caller's stream
-  CKB(cudaStreamWaitEvent(s, b->ev_in, 0));
-  CKB(cudaEventRecord(b->e0, s));
-  if (b->use_graph) {
-    if (!b->exec) {
-      CKB(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      const int r = batch_enqueue(b);
-      cudaGraph_t g = nullptr;
-      const cudaError_t ec = cudaStreamEndCapture(s, &g);
-      if (r != HFX_OK) {
-        if (g) cudaGraphDestroy(g);
-        return r;
-      }
-      if (ec != cudaSuccess) return b->fail(HFX_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
-      b->graph = g;
-      CKB(cudaGraphInstantiate(&b->exec, g, 0));
-    }
-    CKB(cudaGraphLaunch(b->exec, s));
-  } else {
-    const int r = batch_enqueue(b);
-    if (r != HFX_OK) return r;
-  }
-  CKB(cudaEventRecord(b->e1, s));
-  CKB(cudaEventRecord(b->ev_out, s));  // later work on the caller's stream sees K and E_K
-  CKB(cudaStreamWaitEvent(b->user, b->ev_out, 0));
-  b->ran = true;
-  return HFX_OK;
-}
-
-extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* const* K, const int* ld) {
-  if (!b || !P || !K) return HFX_ERR_ARG;
-  if (b->ran) CKB(cudaStreamSynchronize(b->stream));
-  CKB(cudaStreamSynchronize(b->user));
-  batch_set_buffers(b, P, K, ld);
-  cudaStream_t s = b->stream;
-  CKB(cudaMemcpyAsync(b->d_launch, b->h_launch, sizeof(EriLaunch) * 21 * b->n, cudaMemcpyHostToDevice, s));
-  CKB(cudaMemcpyAsync(b->d_sys, b->h_sys, sizeof(BatchSys) * b->n, cudaMemcpyHostToDevice, s));
-  CKB(launch_batch_prologue(b->d_sys, b->n, b->n_sm, b->skip_zero || b->mixed, s));
-  cudaEvent_t t0, t1;
-  CKB(cudaEventCreate(&t0));
-  CKB(cudaEventCreate(&t1));
-  for (int cp = 0; cp < 21; ++cp) {
-    if (b->total[cp] == 0) continue;
-    struct Cand { int g32, chunk; };
-    std::vector<Cand> cands;
-    for (int c : {4, 8, 16, 32}) cands.push_back({1, c});
-    if (!b->mixed && eri_group_size(cp) == 1)
-      for (int c : {128, 256, 512, 1024}) cands.push_back({0, c});
-    double best = 1e30;
-    Cand bc = {b->g32[cp], b->chunk[cp]};
-    for (const Cand& cd : cands) {
-      b->g32[cp] = cd.g32;
-      b->chunk[cp] = cd.chunk;
-      float ms = 0.f, tot = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {  // first repetition warms caches; keep the second
-        CKB(cudaMemsetAsync(b->d_work + cp, 0, sizeof(unsigned long long), s));
-        const EriLaunch L = batch_class_launch(b, cp);
-        CKB(cudaEventRecord(t0, s));
-        CKB(eri_launch(L, cp, 0, batch_grid(b, cp), s, b->g32[cp], b->mixed && b->g32[cp], true));
-        CKB(cudaEventRecord(t1, s));
-        CKB(cudaEventSynchronize(t1));
-        CKB(cudaEventElapsedTime(&ms, t0, t1));
-        tot = ms;
-      }
-      if (tot < best) {
-        best = tot;
-        bc = cd;
-      }
-    }
-    b->g32[cp] = bc.g32;
-    b->chunk[cp] = bc.chunk;
-    b->tune_ms[cp] = best;
-  }
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
-  // a captured graph holds the previous choices
-  if (b->exec) {
-    cudaGraphExecDestroy(b->exec);
-    b->exec = nullptr;
-  }
-  if (b->graph) {
-    cudaGraphDestroy(b->graph);
-    b->graph = nullptr;
-  }
-  CKB(cudaStreamSynchronize(s));
-  return HFX_OK;
-}
-
-extern "C" int hfx_batch_get_stats(hfx_batch* b, hfx_batch_stats* out) {
-  if (!b || !out) return HFX_ERR_ARG;
-  CKB(cudaStreamSynchronize(b->stream));
-  std::memset(out, 0, sizeof(*out));
-  for (int cp = 0; cp < 21; ++cp) {
-    out->n_quartets += b->total[cp];
-    out->group_size_class[cp] = b->g32[cp] ? 32 : 1;
-    out->chunk_class[cp] = b->chunk[cp];
-    out->tune_ms_class[cp] = b->tune_ms[cp];
-  }
-  float ms = 0.f;
-  if (b->ran && cudaEventElapsedTime(&ms, b->e0, b->e1) == cudaSuccess) out->ms_last = ms;
-  return HFX_OK;
-}
-
-extern "C" int hfx_build_K_batched(hfx_ctx* const* ctxs, const double* const* P, double* const* K, const int* ld,
-                                   int n) {
-  hfx_batch* b = nullptr;
-  int r = hfx_batch_create(&b, ctxs, n, nullptr);
-  if (r != HFX_OK) return r;
-  hfx_batch_set_graph(b, 0);
-  r = hfx_batch_run(b, P, K, ld);
-  if (r == HFX_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) r = HFX_ERR_CUDA;
-  hfx_batch_free(b);
-  return r;
-}

@@ -235,8 +235,13 @@ __device__ __forceinline__ void g32_range(const EriLaunch& Ls, long long q0, lon
     const double pm = pmax4(Ls, sa, sb, sc, sd);
     if (Ls.skip_zero && pm == 0.0) continue;
     // mixed precision: FP32 recurrences when the Schwarz bound times the largest density
-    // element the quartet touches is below fp32_tau (warp-uniform decision)
-    const bool f32 = MIXED && Ls.fp32_ok && __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pm < Ls.fp32_tau;
+    // element the quartet touches (or the largest of all of P) is below fp32_tau
+    // (warp-uniform decision)
+    bool f32 = false;
+    if (MIXED && Ls.fp32_ok) {
+      const double pf = Ls.pglob ? __ldg(Ls.pglob) : pm;
+      f32 = __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pf < Ls.fp32_tau;
+    }
     const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
     int ne;
     if (MIXED && f32)
@@ -285,18 +290,18 @@ __device__ __forceinline__ void for_each_range(const EriLaunch& L, long long wid
     const long long c1 = min(c0 + L.chunk, total);
     if constexpr (!BATCH) {
       f(L, L.q_begin + c0, L.q_begin + c1);
-      continue;
-    }
-    while (c0 < c1) {
-      int lo = 0, hi = L.n_sys - 1;  // last s with seg[s] <= c0
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(L.seg + mid) <= c0) lo = mid; else hi = mid - 1;
+    } else {
+      while (c0 < c1) {
+        int lo = 0, hi = L.n_sys - 1;  // last s with seg[s] <= c0
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (__ldg(L.seg + mid) <= c0) lo = mid; else hi = mid - 1;
+        }
+        const long long e = min(c1, __ldg(L.seg + lo + 1));
+        const EriLaunch& Ls = L.batch[lo];
+        f(Ls, Ls.q_begin + (c0 - __ldg(L.seg + lo)), Ls.q_begin + (e - __ldg(L.seg + lo)));
+        c0 = e;
       }
-      const long long e = min(c1, __ldg(L.seg + lo + 1));
-      const EriLaunch& Ls = L.batch[lo];
-      f(Ls, Ls.q_begin + (c0 - __ldg(L.seg + lo)), Ls.q_begin + (e - __ldg(L.seg + lo)));
-      c0 = e;
     }
   }
 }

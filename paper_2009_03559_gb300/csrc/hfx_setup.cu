@@ -206,16 +206,26 @@ __global__ void k_gather_bounds(RowTable rt, const long long* __restrict__ qoff,
 }
 
 // max |P| over each shell-pair block (I, J): one thread per block
+// max over a warp, then one atomic per warp into *out (values >= 0, so the order of
+// their bit patterns as unsigned integers is their numeric order)
+__device__ __forceinline__ void warp_max_into(double m, double* out) {
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(m));
+}
+
 __global__ void k_pmax(int ns, const int* __restrict__ bf_off, const int* __restrict__ l,
-                       const double* __restrict__ P, int ld, double* __restrict__ pmax) {
+                       const double* __restrict__ P, int ld, double* __restrict__ pmax, double* pglob) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)ns * ns) return;
-  const int I = (int)(t / ns), J = (int)(t - (long long)I * ns);
-  const int oi = bf_off[I], oj = bf_off[J], ni = 2 * l[I] + 1, nj = 2 * l[J] + 1;
   double m = 0.0;
-  for (int a = 0; a < ni; ++a)
-    for (int b = 0; b < nj; ++b) m = fmax(m, fabs(P[(size_t)(oi + a) * ld + oj + b]));
-  pmax[t] = m;
+  if (t < (long long)ns * ns) {
+    const int I = (int)(t / ns), J = (int)(t - (long long)I * ns);
+    const int oi = bf_off[I], oj = bf_off[J], ni = 2 * l[I] + 1, nj = 2 * l[J] + 1;
+    for (int a = 0; a < ni; ++a)
+      for (int b = 0; b < nj; ++b) m = fmax(m, fabs(P[(size_t)(oi + a) * ld + oj + b]));
+    pmax[t] = m;
+  }
+  if (pglob) warp_max_into(m, pglob);  // blockDim is a multiple of 32: whole warps get here
 }
 
 // ---------------------------------------------------------------------------
@@ -329,6 +339,7 @@ __global__ void k_fma_chain(T* out, int iters, T a, T b) {
 // ---------------------------------------------------------------------------
 __global__ void k_batch_zero(const BatchSys* __restrict__ sys) {
   const BatchSys b = sys[blockIdx.y];
+  if (b.pglob && blockIdx.x == 0 && threadIdx.x == 0) *b.pglob = 0.0;
   const long long nn = (long long)b.n * b.n;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t / b.n), j = (int)(t - (long long)i * b.n);
@@ -339,14 +350,22 @@ __global__ void k_batch_zero(const BatchSys* __restrict__ sys) {
 __global__ void k_batch_pmax(const BatchSys* __restrict__ sys) {
   const BatchSys b = sys[blockIdx.y];
   const long long nn = (long long)b.ns * b.ns;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // every thread runs the same number of rounds, so whole warps reach the reduction
+  const long long rounds = (nn + stride - 1) / stride;
+  double mg = 0.0;
+  for (long long k = 0; k < rounds; ++k) {
+    const long long t = k * stride + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nn) continue;
     const int I = (int)(t / b.ns), J = (int)(t - (long long)I * b.ns);
     const int oi = b.bf_off[I], oj = b.bf_off[J], ni = 2 * b.l[I] + 1, nj = 2 * b.l[J] + 1;
     double m = 0.0;
     for (int a = 0; a < ni; ++a)
       for (int c = 0; c < nj; ++c) m = fmax(m, fabs(b.P[(size_t)(oi + a) * b.ld + oj + c]));
     b.pmax[t] = m;
+    mg = fmax(mg, m);
   }
+  if (b.pglob) warp_max_into(mg, b.pglob);
 }
 
 __global__ void k_batch_symmetrize(const BatchSys* __restrict__ sys) {
@@ -377,13 +396,13 @@ __global__ void k_batch_symmetrize(const BatchSys* __restrict__ sys) {
   }
 }
 
-// one block per system: compensated sum of P K
-__global__ void k_batch_trace(const BatchSys* __restrict__ sys) {
-  const BatchSys b = sys[blockIdx.x];
+// compensated partial sums of P K: blockIdx.y = system, kBatchPart blocks per system
+__global__ void k_batch_trace_partial(const BatchSys* __restrict__ sys) {
+  const BatchSys b = sys[blockIdx.y];
   __shared__ double ss[256], cc[256];
   double s = 0.0, c = 0.0;
   const long long nn = (long long)b.n * b.n;
-  for (long long t = threadIdx.x; t < nn; t += blockDim.x) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t / b.n), j = (int)(t - (long long)i * b.n);
     double e;
     two_sum(s, b.P[(size_t)i * b.ld + j] * b.K[(size_t)i * b.ld + j], s, e);
@@ -393,6 +412,27 @@ __global__ void k_batch_trace(const BatchSys* __restrict__ sys) {
   cc[threadIdx.x] = c;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double e;
+      two_sum(ss[threadIdx.x], ss[threadIdx.x + w], ss[threadIdx.x], e);
+      cc[threadIdx.x] += cc[threadIdx.x + w] + e;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    b.part[2 * blockIdx.x] = ss[0];
+    b.part[2 * blockIdx.x + 1] = cc[0];
+  }
+}
+
+// one block of kBatchPart threads per system: E_K from the partial sums
+__global__ void k_batch_trace_final(const BatchSys* __restrict__ sys) {
+  const BatchSys b = sys[blockIdx.x];
+  __shared__ double ss[kBatchPart], cc[kBatchPart];
+  ss[threadIdx.x] = b.part[2 * threadIdx.x];
+  cc[threadIdx.x] = b.part[2 * threadIdx.x + 1];
+  __syncthreads();
+  for (int w = kBatchPart / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
       double e;
       two_sum(ss[threadIdx.x], ss[threadIdx.x + w], ss[threadIdx.x], e);
@@ -521,10 +561,14 @@ cudaError_t launch_finalize(int n, int ld, const double* P, double* K, double* p
 }
 
 cudaError_t launch_pmax(int ns, const int* bf_off, const int* l, const double* P, int ld, double* pmax,
-                        cudaStream_t s) {
+                        double* pglob, cudaStream_t s) {
   const long long n = (long long)ns * ns;
   if (n <= 0) return cudaSuccess;
-  k_pmax<<<nblk(n, 256), 256, 0, s>>>(ns, bf_off, l, P, ld, pmax);
+  if (pglob) {
+    cudaError_t e = cudaMemsetAsync(pglob, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+  }
+  k_pmax<<<nblk(n, 256), 256, 0, s>>>(ns, bf_off, l, P, ld, pmax, pglob);
   return cudaGetLastError();
 }
 
@@ -538,7 +582,8 @@ cudaError_t launch_batch_prologue(const BatchSys* sys, int n, int n_sm, bool pma
 cudaError_t launch_batch_epilogue(const BatchSys* sys, int n, int n_sm, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_batch_symmetrize<<<dim3(n_sm, n), dim3(32, 8), 0, s>>>(sys);
-  k_batch_trace<<<n, 256, 0, s>>>(sys);
+  k_batch_trace_partial<<<dim3(kBatchPart, n), 256, 0, s>>>(sys);
+  k_batch_trace_final<<<n, kBatchPart, 0, s>>>(sys);
   return cudaGetLastError();
 }
 

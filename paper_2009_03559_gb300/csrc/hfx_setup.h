@@ -6,14 +6,18 @@
 namespace hfx {
 
 // One system of a batched K build (device table; read by the batched kernels).
+// One system of a batched build: its matrices, shell data and per-build scratch.
+constexpr int kBatchPart = 64;  // partial sums of E_K per system (2 doubles each)
 struct BatchSys {
   const double* P;
   double* K;
   int n, ld, ns;
   const int* bf_off;
   const int* l;
-  double* pmax;
-  double* energy;
+  double* pmax;    // ns x ns block maxima of |P|
+  double* energy;  // E_K
+  double* part;    // 2 * kBatchPart doubles
+  double* pglob;   // max |P| over the matrix, or NULL when not needed
 };
 
 // Rows of the quartet task list: class pair cp = hi(hi+1)/2 + lo owns rows
@@ -55,8 +59,9 @@ cudaError_t launch_count(int n_rows, const RowTable& rt, const double* Qs, doubl
 cudaError_t launch_gather_bounds(const RowTable& rt, const long long* qoff, long long* out, cudaStream_t s);
 cudaError_t launch_finalize(int n, int ld, const double* P, double* K, double* part, int n_part, double* energy,
                             cudaStream_t s);
+// block maxima of |P| per shell pair; with pglob != NULL also the maximum over all of P
 cudaError_t launch_pmax(int ns, const int* bf_off, const int* l, const double* P, int ld, double* pmax,
-                        cudaStream_t s);
+                        double* pglob, cudaStream_t s);
 cudaError_t launch_batch_prologue(const BatchSys* sys, int n, int n_sm, bool pmax, cudaStream_t s);
 cudaError_t launch_batch_epilogue(const BatchSys* sys, int n, int n_sm, cudaStream_t s);
 cudaError_t fma_peak(double* fp64_tflops, double* fp32_tflops);

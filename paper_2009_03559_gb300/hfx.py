@@ -16,7 +16,9 @@ LIB_PATH = os.path.join(HERE, "_build", "libhfx.so")
 
 HFX_FP64, HFX_MIXED = 0, 1
 HFX_SCHED_QUARTET, HFX_SCHED_PAIR, HFX_SCHED_DYNAMIC = 0, 1, 2
-ERR_NAMES = {0: "OK", -1: "ARG", -2: "UNSUPPORTED_L", -3: "OOM", -4: "CUDA", -5: "STATE", -6: "TIMEOUT"}
+ERR_NAMES = {0: "OK", -1: "ARG", -2: "UNSUPPORTED_L", -3: "OOM", -4: "CUDA", -5: "STATE", -6: "TIMEOUT",
+             -7: "ADMISSION"}
+REQ_DONE, REQ_QUEUED, REQ_RUNNING = 0, 1, 2
 
 PAIR_CLASSES = ["ss", "ps", "pp", "ds", "dp", "dd"]
 QUARTET_CLASSES = [f"({PAIR_CLASSES[hi]}|{PAIR_CLASSES[lo]})" for hi in range(6) for lo in range(hi + 1)]
@@ -28,7 +30,32 @@ class Options(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("schwarz_tau", ctypes.c_double), ("rcut_bohr", ctypes.c_double),
                 ("prim_tau", ctypes.c_double), ("fp32_tau", ctypes.c_double), ("precision", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("skip_zero_p", ctypes.c_int), ("fp32_class_mask", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("fp32_pmax_global", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget_gb", ctypes.c_double), ("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("system_id", ctypes.c_int32),
+                ("step_size", ctypes.c_int32), ("pad", ctypes.c_int32), ("energy", ctypes.c_double),
+                ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double),
+                ("ms_step", ctypes.c_double), ("n_quartets", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("n_submitted", "n_done", "n_failed", "n_steps", "n_queued",
+                                              "n_running", "quartets_done", "bytes_resident", "bytes_requests",
+                                              "bytes_peak")] + \
+               [("max_step_size", ctypes.c_int32), ("max_steps_inflight", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
@@ -60,13 +87,14 @@ class Stats(ctypes.Structure):
 class BatchStats(ctypes.Structure):
     _fields_ = [("n_quartets", ctypes.c_int64), ("ms_last", ctypes.c_double),
                 ("group_size_class", ctypes.c_int32 * 21), ("chunk_class", ctypes.c_int32 * 21),
-                ("tune_ms_class", ctypes.c_double * 21)]
+                ("tune_ms_class", ctypes.c_double * 21), ("tune_window_class", ctypes.c_int64 * 21)]
 
     def as_dict(self):
         return {"n_quartets": int(self.n_quartets), "ms_last": float(self.ms_last),
                 "group_size_class": [int(x) for x in self.group_size_class],
                 "chunk_class": [int(x) for x in self.chunk_class],
-                "tune_ms_class": [float(x) for x in self.tune_ms_class]}
+                "tune_ms_class": [float(x) for x in self.tune_ms_class],
+                "tune_window_class": [int(x) for x in self.tune_window_class]}
 
 
 _lib = None
@@ -119,6 +147,8 @@ def load_library(path: str = LIB_PATH):
     L.hfx_batch_run.restype = ctypes.c_int
     L.hfx_batch_set_graph.argtypes = [vp, ctypes.c_int]
     L.hfx_batch_set_graph.restype = ctypes.c_int
+    L.hfx_batch_set_tune_target.argtypes = [vp, ctypes.c_double]
+    L.hfx_batch_set_tune_target.restype = ctypes.c_int
     L.hfx_batch_get_stats.argtypes = [vp, ctypes.POINTER(BatchStats)]
     L.hfx_batch_get_stats.restype = ctypes.c_int
     L.hfx_batch_free.argtypes = [vp]
@@ -129,6 +159,31 @@ def load_library(path: str = LIB_PATH):
     L.hfx_energy_noalloc.restype = ctypes.c_int
     L.hfx_measure_fma_peak.argtypes = [dp, dp]
     L.hfx_measure_fma_peak.restype = ctypes.c_int
+    L.hfx_device_bytes.argtypes = [vp]
+    L.hfx_device_bytes.restype = ctypes.c_int64
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    L.hfx_server_default_options.argtypes = [ctypes.POINTER(ServerOptions)]
+    L.hfx_server_default_options.restype = None
+    L.hfx_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServerOptions)]
+    L.hfx_server_create.restype = ctypes.c_int
+    L.hfx_server_add_system.argtypes = [vp, vp, ip]
+    L.hfx_server_add_system.restype = ctypes.c_int
+    L.hfx_serve_submit.argtypes = [vp, ctypes.c_int, vp, vp, vp, u64p]
+    L.hfx_serve_submit.restype = ctypes.c_int
+    L.hfx_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
+    L.hfx_serve_poll.restype = ctypes.c_int
+    L.hfx_serve_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(Result)]
+    L.hfx_serve_wait.restype = ctypes.c_int
+    L.hfx_serve_progress.argtypes = [vp]
+    L.hfx_serve_progress.restype = ctypes.c_int
+    L.hfx_serve_drain.argtypes = [vp, ctypes.c_double]
+    L.hfx_serve_drain.restype = ctypes.c_int
+    L.hfx_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    L.hfx_server_get_stats.restype = ctypes.c_int
+    L.hfx_server_last_error.argtypes = [vp]
+    L.hfx_server_last_error.restype = ctypes.c_char_p
+    L.hfx_server_free.argtypes = [vp]
+    L.hfx_server_free.restype = None
     _lib = L
     return L
 
@@ -171,7 +226,8 @@ class HFX:
     """
 
     def __init__(self, system, stream=None, tau=None, rcut=None, omega=None, schedule=HFX_SCHED_DYNAMIC,
-                 prim_tau=None, skip_zero_p=True, precision=HFX_FP64, fp32_tau=None, fp32_class_mask=None):
+                 prim_tau=None, skip_zero_p=True, precision=HFX_FP64, fp32_tau=None, fp32_class_mask=None,
+                 fp32_pmax_global=False):
         import torch  # device memory and streams only
         if not torch.cuda.is_available():
             raise RuntimeError("HFX needs a CUDA device; there is no CPU path")
@@ -192,6 +248,7 @@ class HFX:
             o.fp32_tau = fp32_tau
         if fp32_class_mask is not None:
             o.fp32_class_mask = fp32_class_mask
+        o.fp32_pmax_global = 1 if fp32_pmax_global else 0
         self.options = o
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         xyz, sa, sl, sn, al, co = system.basis_arrays()
@@ -261,6 +318,9 @@ class HFX:
             raise HFXError(int(r), self.L.hfx_last_error(self.h).decode())
         return a[:r], b[:r], q[:r]
 
+    def device_bytes(self) -> int:
+        return int(self.L.hfx_device_bytes(self.h))
+
     def sm_busy_ns(self, max_n=1024):
         out = np.zeros(max_n)
         r = self.L.hfx_get_cta_busy(self.h, _dp(out), max_n)
@@ -311,7 +371,9 @@ class Batch:
         if rc != 0:
             raise HFXError(rc, self.L.hfx_last_error(None).decode())
 
-    def tune(self, Ps, Ks):
+    def tune(self, Ps, Ks, target_ms=None):
+        if target_ms is not None:
+            self._check(self.L.hfx_batch_set_tune_target(self.h, ctypes.c_double(target_ms)))
         pP, pK, ld, keep = self._args(Ps, Ks)
         self._check(self.L.hfx_batch_tune(self.h, pP, pK, ld))
 
@@ -329,6 +391,88 @@ class Batch:
         if getattr(self, "h", None):
             self.L.hfx_batch_free(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request loop with continuous batching over registered ``HFX`` contexts (the C
+    server in hfx_batch.cu; this class only marshals arguments)."""
+
+    def __init__(self, hbm_budget_gb=120.0, max_inflight=4, max_batch=16, precision=HFX_FP64):
+        self.L = load_library()
+        o = ServerOptions()
+        self.L.hfx_server_default_options(ctypes.byref(o))
+        o.hbm_budget_gb = float(hbm_budget_gb)
+        o.max_inflight = int(max_inflight)
+        o.max_batch = int(max_batch)
+        o.precision = int(precision)
+        h = ctypes.c_void_p()
+        rc = self.L.hfx_server_create(ctypes.byref(h), ctypes.byref(o))
+        if rc != 0:
+            raise HFXError(rc, self.L.hfx_last_error(None).decode())
+        self.h = h
+        self.contexts = []
+        self._keep = {}
+
+    def _check(self, rc):
+        if rc < 0:
+            raise HFXError(rc, self.L.hfx_server_last_error(self.h).decode())
+        return rc
+
+    def add_system(self, ctx) -> int:
+        i = ctypes.c_int()
+        self._check(self.L.hfx_server_add_system(self.h, ctx.h, ctypes.byref(i)))
+        self.contexts.append(ctx)
+        return i.value
+
+    def submit(self, system_id, P, K_out, stream=None) -> int:
+        """P, K_out: torch float64 tensors (CUDA, or pinned CPU), n x n contiguous.  They
+        are kept alive here until the request's result has been read."""
+        import torch
+        t = ctypes.c_uint64()
+        if stream is None and P.is_cuda:
+            stream = torch.cuda.current_stream()
+        st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        self._check(self.L.hfx_serve_submit(self.h, int(system_id), ctypes.c_void_p(P.data_ptr()),
+                                            ctypes.c_void_p(K_out.data_ptr()), st, ctypes.byref(t)))
+        self._keep[t.value] = (P, K_out)
+        return t.value
+
+    def poll(self, ticket) -> dict:
+        r = Result()
+        self._check(self.L.hfx_serve_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(r)))
+        if r.status <= 0:
+            self._keep.pop(ticket, None)
+        return r.as_dict()
+
+    def wait(self, ticket, timeout_ms=-1.0) -> dict:
+        r = Result()
+        self._check(self.L.hfx_serve_wait(self.h, ctypes.c_uint64(ticket), ctypes.c_double(timeout_ms),
+                                          ctypes.byref(r)))
+        self._keep.pop(ticket, None)
+        return r.as_dict()
+
+    def progress(self) -> int:
+        return self._check(self.L.hfx_serve_progress(self.h))
+
+    def drain(self, timeout_ms=-1.0):
+        self._check(self.L.hfx_serve_drain(self.h, ctypes.c_double(timeout_ms)))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        self._check(self.L.hfx_server_get_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.hfx_server_free(self.h)
+            self.h = None
+            self._keep.clear()
 
     def __del__(self):
         try:
