@@ -13,6 +13,15 @@ N > 1 (torchrun): independent replicas of the same workload, one per GPU ("scali
 "weak"); the K build has no exchange step between GPUs.  --impl reference times the
 CPU oracle (the only other implementation: there is no reference code) on the host
 cores for a bounded sample of the same workload.
+
+Other workloads (one JSON line each, rank 0, one GPU; reports beside the main line):
+  --workload batch32     32 systems (8..128 atoms, cluster or diamond) in one batched,
+                         autotuned build replayed from a CUDA graph, vs the same systems
+                         built one by one (plain FP64)
+  --workload diamond216  216-atom diamond (2808 functions): plain FP64 vs mixed precision
+  --workload serve       request stream (Poisson arrivals, systems from a seeded pool)
+                         through the continuous-batching server (mixed precision) vs the
+                         same stream built one request at a time (plain FP64, FIFO)
 """
 from __future__ import annotations
 
@@ -43,6 +52,16 @@ def workload_desc(s, mixed=False, fp32_classes="all"):
 WORKLOAD = ("diamond-64 DZP-like: 64 atoms (2x2x2 cells, a=10.26 bohr), 320 shells s,s,p,p,d, "
             "832 spherical functions, 3 primitives/shell, omega=0.11, r_c=6 bohr, tau=1e-8, "
             "P truncated beyond 10 bohr; plain FP64")
+
+
+def max_over_ranks(value, pg):
+    """Maximum of a host float over the ranks of the default process group (CUDA tensor
+    for NCCL, CPU tensor for gloo)."""
+    import torch
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_info():
@@ -137,20 +156,23 @@ def reference_arm(args, ws, rank):
 
 
 def oracle_sample(S, s, n, seed=777):
-    """Seeded uniform sample of kept canonical quartets (I>=J, K>=L, IJ>=KL)."""
+    """Seeded uniform sample of kept canonical quartets (I>=J, K>=L, IJ>=KL): pairs of
+    kept shell pairs drawn uniformly, kept if their Schwarz product passes tau."""
     Q, cut, kept, qmax = S.export()
-    ns = s.n_shells
-    pairs = [(I, J) for I in range(ns) for J in range(I + 1) if kept[I, J]]
-    q = np.array([Q[I, J] for I, J in pairs])
+    I, J = np.nonzero(np.tril(kept))
+    q = Q[I, J]
     rng = np.random.default_rng(seed)
     out = []
-    while len(out) < n:
-        a, b = rng.integers(0, len(pairs), 2)
-        if b > a:
-            a, b = b, a
-        if q[a] * q[b] >= S.tau:
-            out.append(pairs[a] + pairs[b])
-    return np.array(out, dtype=np.int32)
+    got = 0
+    while got < n:
+        a = rng.integers(0, len(I), 4 * n)
+        b = rng.integers(0, len(I), 4 * n)
+        hi, lo = np.maximum(a, b), np.minimum(a, b)
+        ok = q[hi] * q[lo] >= S.tau
+        hi, lo = hi[ok], lo[ok]
+        out.append(np.stack([I[hi], J[hi], I[lo], J[lo]], axis=1))
+        got += len(hi)
+    return np.ascontiguousarray(np.concatenate(out)[:n], dtype=np.int32)
 
 
 def cpu_baseline(args):
@@ -168,13 +190,190 @@ def cpu_baseline(args):
                       f"integrals only, {dt:.1f} s"}
 
 
+def _evt(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_batch32(args, torch, hfx, inputs):
+    """32 independent systems: one batched, autotuned build replayed from a CUDA graph vs
+    the same systems built one by one through the single-system entry point."""
+    systems = inputs.config2_systems()
+    ctxs = [hfx.HFX(s).build_pairs() for s, P in systems]
+    Ps = [torch.from_numpy(P).cuda() for s, P in systems]
+    Ks = [torch.empty_like(P) for P in Ps]
+    Ks1 = [torch.empty_like(P) for P in Ps]
+    nq = sum(c.stats()["n_quartets"] for c in ctxs)
+    torch.cuda.synchronize()
+    a, b = _evt(torch)
+    # one by one (plain single-system path), one pass after a small warm-up
+    ctxs[11].build_K(Ps[11], Ks1[11])
+    a.record()
+    for c, P, K in zip(ctxs, Ps, Ks1):
+        c.build_K(P, K)
+    b.record()
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b)
+    e_seq = [c.energy() for c in ctxs]
+    bt = hfx.Batch(ctxs)
+    t0 = time.perf_counter()
+    bt.tune(Ps, Ks)
+    tune_s = time.perf_counter() - t0
+    bt.run(Ps, Ks)  # capture + first replay
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    a.record()
+    bt.run(Ps, Ks)
+    b.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    bat_ms = a.elapsed_time(b)
+    e_bat = [c.energy() for c in ctxs]
+    dk = max(torch.abs(x - y).max().item() for x, y in zip(Ks, Ks1))
+    st = bt.stats()
+    print(json.dumps({
+        "metric": METRIC, "workload": "batch32", "value": nq / (bat_ms * 1e-3), "unit": "quartets/s",
+        "ms_per_step": bat_ms, "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "32 systems, atoms uniform in 8..128, cluster (s,p; tau 1e-10, no cutoff) or "
+                               "diamond (s,s,p,p,d; tau 1e-8, r_c 6 bohr, P truncated beyond 10 bohr) by a "
+                               "seeded coin; plain FP64",
+                   "quartets": nq, "systems": [[s.kind, s.n_atoms, s.n_bf] for s, P in systems]},
+        "one_by_one": {"ms": seq_ms, "quartets_per_s": nq / (seq_ms * 1e-3)},
+        "speedup_vs_one_by_one": seq_ms / bat_ms,
+        "tuner": {"seconds": tune_s, "group_size_class": st["group_size_class"], "chunk_class": st["chunk_class"],
+                  "window_class": st["tune_window_class"]},
+        "max_abs_dK_batched_vs_single": dk,
+        "max_abs_dE_batched_vs_single": max(abs(x - y) for x, y in zip(e_seq, e_bat)),
+        "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"]},
+    }), flush=True)
+
+
+def run_diamond216(args, torch, hfx, inputs):
+    """216-atom diamond: plain FP64 build vs mixed precision (FP32 recurrences for quartets
+    with Q_IJ Q_KL max|P blocks| < fp32_tau)."""
+    s, P_np = inputs.config3()
+    P = torch.from_numpy(P_np).cuda()
+    out = {}
+    Ks = {}
+    for name, prec, mask in (("fp64", hfx.HFX_FP64, None), ("mixed_sp", hfx.HFX_MIXED, hfx.SP_CLASS_MASK),
+                             ("mixed_all", hfx.HFX_MIXED, (1 << 21) - 1)):
+        h = hfx.HFX(s, precision=prec, fp32_class_mask=mask, fp32_tau=args.fp32_tau).build_pairs()
+        h.set_timing(True)
+        K = torch.empty_like(P)
+        h.build_K(P, K)  # warm-up
+        torch.cuda.synchronize()
+        a, b = _evt(torch)
+        a.record()
+        h.build_K(P, K)
+        b.record()
+        torch.cuda.synchronize()
+        st = h.stats()
+        ms = a.elapsed_time(b)
+        out[name] = {"ms": ms, "quartets_per_s": st["n_quartets"] / (ms * 1e-3), "energy": h.energy(),
+                     "quartets_evaluated": sum(st["quartets_evaluated_class"]),
+                     "quartets_fp32": sum(st["quartets_fp32_class"]),
+                     "fp64_flops": st["flops_fp64"], "fp32_flops": st["flops_fp32"]}
+        Ks[name] = K
+        n_q = st["n_quartets"]
+        h.close()
+    for name in ("mixed_sp", "mixed_all"):
+        d = (Ks[name] - Ks["fp64"]).abs()
+        out[name]["max_abs_dK_vs_fp64"] = d.max().item()
+        out[name]["rms_dK_vs_fp64"] = float(torch.sqrt((d * d).mean()).item())
+        out[name]["abs_dE_vs_fp64"] = abs(out[name]["energy"] - out["fp64"]["energy"])
+    print(json.dumps({
+        "metric": METRIC, "workload": "diamond216", "value": out["mixed_sp"]["quartets_per_s"],
+        "unit": "quartets/s", "ms_per_step": out["mixed_sp"]["ms"], "n_gpus": 1, "steps": 1, "warmup": 1,
+        "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": workload_desc(s, True, "sp"), "quartets": n_q, "fp32_tau": args.fp32_tau},
+        "runs": out}), flush=True)
+
+
+def run_serve(args, torch, hfx, inputs):
+    """The request stream through the continuous-batching server (mixed precision) and,
+    with the same arrivals, one request at a time through the plain FP64 single-system
+    path (FIFO).  Latency = device completion - submission."""
+    pool, reqs = inputs.config4_requests(n_requests=args.requests, n_hi=args.serve_max_atoms)
+    used = sorted({w for _, w, _ in reqs})
+    sysobj = {w: inputs.make_system(pool[w][0], pool[w][1], pool[w][2]) for w in used}
+    P_dev = [torch.from_numpy(inputs.density_matrix(sysobj[w], seed=sd,
+                                                    truncate_bohr=inputs.truncation_for(sysobj[w].kind))).cuda()
+             for _, w, sd in reqs]
+    K_srv = [torch.empty_like(P) for P in P_dev]
+    K_one = [torch.empty_like(P) for P in P_dev]
+    arrivals = [t for t, _, _ in reqs]
+    # plain arm: FP64 contexts, one build at a time in arrival order
+    plain = {w: hfx.HFX(sysobj[w]).build_pairs() for w in used}
+    nq = {w: plain[w].stats()["n_quartets"] for w in used}
+    plain[used[0]].build_K(P_dev[0], K_one[0])
+    torch.cuda.synchronize()
+    lat1, e_one, t0 = [], [], time.perf_counter()
+    for i, (ta, w, sd) in enumerate(reqs):
+        while time.perf_counter() - t0 < ta:
+            time.sleep(1e-4)
+        plain[w].build_K(P_dev[i], K_one[i])
+        torch.cuda.synchronize()
+        lat1.append(1e3 * (time.perf_counter() - t0 - ta))
+        e_one.append(plain[w].energy())
+    span1 = time.perf_counter() - t0
+    # served arm
+    srv = hfx.Server(hbm_budget_gb=120.0, max_inflight=4, max_batch=16, precision=hfx.HFX_MIXED)
+    mixed_ctx = {w: hfx.HFX(sysobj[w], precision=hfx.HFX_MIXED).build_pairs() for w in used}
+    sid = {w: srv.add_system(mixed_ctx[w]) for w in used}
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    tickets, t0 = [], time.perf_counter()
+    for i, (ta, w, sd) in enumerate(reqs):
+        while time.perf_counter() - t0 < ta:
+            srv.progress()
+            time.sleep(1e-4)
+        tickets.append(srv.submit(sid[w], P_dev[i], K_srv[i]))
+    srv.drain()
+    span2 = time.perf_counter() - t0
+    ck = clocks.stop()
+    res = [srv.poll(t) for t in tickets]
+    st = srv.stats()
+    lat2 = [r["t_done_ms"] - r["t_submit_ms"] for r in res]
+    done2 = max(r["t_done_ms"] for r in res) - min(r["t_submit_ms"] for r in res)
+    total_q = sum(nq[w] for _, w, _ in reqs)
+    dk = max(torch.abs(a - b).max().item() for a, b in zip(K_srv, K_one))
+    de = max(abs(r["energy"] - e) for r, e in zip(res, e_one))
+    pct = lambda v, q: float(np.percentile(v, q))
+    print(json.dumps({
+        "metric": METRIC, "workload": "serve", "value": total_q / (done2 * 1e-3), "unit": "quartets/s",
+        "p50_ms": pct(lat2, 50), "p99_ms": pct(lat2, 99), "n_gpus": 1, "higher_is_better": True,
+        "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": f"first {args.requests} requests of a Poisson stream (50 req/s), systems drawn "
+                               f"from a seeded pool of 64 (atoms log-uniform in 16..{args.serve_max_atoms}, "
+                               "cluster or diamond), fresh P per request; server: 4 stream slots, batches of "
+                               "<= 16, 120 GB admission budget, mixed precision (s,p classes FP32 below 1e-6)",
+                   "requests": args.requests, "systems_used": len(used), "quartets": total_q,
+                   "arrival_span_s": arrivals[-1]},
+        "served": {"quartets_per_s": total_q / (done2 * 1e-3), "span_s": done2 * 1e-3,
+                   "p50_ms": pct(lat2, 50), "p99_ms": pct(lat2, 99), "steps": st["n_steps"],
+                   "max_step_size": st["max_step_size"], "max_steps_inflight": st["max_steps_inflight"],
+                   "bytes_peak": st["bytes_peak"], "host_span_s": span2},
+        "one_at_a_time_fp64": {"quartets_per_s": total_q / span1, "span_s": span1,
+                               "p50_ms": pct(lat1, 50), "p99_ms": pct(lat1, 99)},
+        "max_abs_dK_served_mixed_vs_fp64": dk, "max_abs_dE_served_mixed_vs_fp64": de,
+        "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"]},
+    }), flush=True)
+    srv.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--ref-sample", type=int, default=60000)
+    ap.add_argument("--ref-sample", type=int, default=2000000,
+                    help="quartets per oracle step (--impl reference) and for the CPU baseline")
+    ap.add_argument("--workload", default="diamond64", choices=["diamond64", "batch32", "diamond216", "serve"])
+    ap.add_argument("--requests", type=int, default=64, help="serve: requests of the stream to run")
+    ap.add_argument("--serve-max-atoms", type=int, default=64, help="serve: largest system of the pool")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--atoms", type=int, default=64,
                     help="diamond piece size (64 = the benchmark workload; smaller for profiler captures)")
@@ -202,6 +401,14 @@ def main():
         torch.cuda.set_device(0)
     from paper_2009_03559_gb300 import hfx, inputs
 
+    if args.workload != "diamond64":
+        if rank == 0:
+            {"batch32": run_batch32, "diamond216": run_diamond216, "serve": run_serve}[args.workload](
+                args, torch, hfx, inputs)
+        if pg:
+            pg.destroy_process_group()
+        return
+
     s, P_np = inputs.config1(args.atoms)
     stream = torch.cuda.Stream()
     mixed = args.precision == "mixed"
@@ -215,13 +422,12 @@ def main():
     n_q = h.stats()["n_quartets"]
     fp64_peak, fp32_peak = hfx.measure_fma_peak()
 
-    # untimed warm-up (last one with per-class timing and counters for the roofline)
+    # untimed warm-up; per-class CUDA events (on the library's stream) and counters stay on
+    # through the timed steps: they time the dominant kernel for the roofline
+    h.set_timing(True)
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
-            h.set_timing(i == args.warmup - 1)
             h.build_K(P, K)
-        st_timed = h.stats()
-        h.set_timing(False)
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -230,12 +436,15 @@ def main():
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
+    class_ms = []
     with torch.cuda.stream(stream):
         for i in range(args.steps):
             flush.fill_(float(i))
             ev[i][0].record(stream)
             h.build_K(P, K)
             ev[i][1].record(stream)
+            st_timed = h.stats()  # waits for this step (outside its events)
+            class_ms.append(st_timed["ms_class"])
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -243,9 +452,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if pg:
-        t = torch.tensor([total_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, pg)
     energy = h.energy()
 
     # end-to-end through the host-buffer entry point (copies inside the timed region)
@@ -258,13 +465,14 @@ def main():
 
     # roofline of the dominant kernel: the warp-cooperative FP64 kernel (classes with G=32)
     from paper_2009_03559_gb300.hfx import QUARTET_CLASSES
-    ms_cls = st_timed["ms_class"]
+    ms_cls = [float(np.mean([c[k] for c in class_ms])) for k in range(21)]
     g32 = [c for c in range(21) if st_timed["group_size_class"][c] == 32 or mixed]
     flops_cls = st_timed["flops_class"]
     dom_ms = sum(ms_cls[c] for c in g32)
     dom_fl = sum(flops_cls[c] for c in g32)
     achieved = dom_fl / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else None
-    launches_per_step = sum(1 for c in range(21) if st_timed["n_quartets_class"][c] > 0) + 3
+    # class launches + density-block maxima + K = A + A^T + two E_K reduction kernels
+    launches_per_step = sum(1 for c in range(21) if st_timed["n_quartets_class"][c] > 0) + 4
 
     if rank == 0:
         line = {
@@ -283,7 +491,8 @@ def main():
             "e2e": {"value": n_q / float(np.median(e2e_t)) if e2e_t else None, "unit": "quartets/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches_per_step * args.steps,
-            "roofline": {"bound": "alu", "kernel": "eri_g32_kernel (FP64 classes with warp groups)",
+            "roofline": {"bound": "alu", "kernel": "eri_g32_kernel (classes with warp groups), "
+                                                   "CUDA events around each class launch over the timed steps",
                          "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
                          "peak_source": "FP64 FMA-chain probe of this run (hfx_measure_fma_peak)"},

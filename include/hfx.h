@@ -140,6 +140,18 @@ int hfx_build_pairs(hfx_ctx* ctx);
  * Errors: HFX_ERR_STATE (no pair list), HFX_ERR_ARG, HFX_ERR_CUDA. */
 int hfx_build_K(hfx_ctx* ctx, const double* P_dev, double* K_dev, int ld);
 
+/* Partition `part` (0 <= part < n_parts) of the same K build: only the quartets of a
+ * contiguous 1/n_parts of every class's screened quartet list (hfx_part_range) contribute.
+ * K_part and E_part = sum P K_part of the parts add up to K and E_K of hfx_build_K; the
+ * parts are independent (no communication), which is how the build shards over GPUs
+ * (one part per GPU, then one sum of the K_part).  Needs the quartet or dynamic
+ * schedule.  Otherwise as hfx_build_K. */
+int hfx_build_K_part(hfx_ctx* ctx, const double* P_dev, double* K_dev, int ld, int part, int n_parts);
+
+/* The range [*q0, *q1) of a list of `count` items that part `part` of n_parts owns:
+ * q0 = floor(count part / n_parts), q1 = floor(count (part + 1) / n_parts).  Host only. */
+int hfx_part_range(int64_t count, int part, int n_parts, int64_t* q0, int64_t* q1);
+
 /* Same computation with host buffers: copies P (host, n_bf x n_bf row-major) to the
  * device, builds K, copies K back into K_host and returns after the copy ends.  The
  * device staging buffers are owned by the context. */

@@ -367,7 +367,33 @@ extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
   return HFX_OK;
 }
 
+extern "C" int hfx_part_range(int64_t count, int part, int n_parts, int64_t* q0, int64_t* q1) {
+  if (!q0 || !q1 || count < 0 || n_parts < 1 || part < 0 || part >= n_parts) return HFX_ERR_ARG;
+  // floor(count * p / n_parts) without overflow for count < 2^62
+  auto cut = [&](int p) {
+    return (count / n_parts) * p + ((count % n_parts) * p) / n_parts;
+  };
+  *q0 = cut(part);
+  *q1 = cut(part + 1);
+  return HFX_OK;
+}
+
+static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int part, int n_parts);
+
 extern "C" int hfx_build_K(hfx_ctx* ctx, const double* P, double* K, int ld) {
+  return build_K_impl(ctx, P, K, ld, 0, 1);
+}
+
+extern "C" int hfx_build_K_part(hfx_ctx* ctx, const double* P, double* K, int ld, int part, int n_parts) {
+  if (!ctx) return HFX_ERR_ARG;
+  if (n_parts < 1 || part < 0 || part >= n_parts)
+    return ctx->fail(HFX_ERR_ARG, "part must be in 0..n_parts-1");
+  if (n_parts > 1 && ctx->opt.schedule == HFX_SCHED_PAIR)
+    return ctx->fail(HFX_ERR_ARG, "partitions split the quartet list: use the quartet or dynamic schedule");
+  return build_K_impl(ctx, P, K, ld, part, n_parts);
+}
+
+static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int part, int n_parts) {
   if (!ctx) return HFX_ERR_ARG;
   if (!ctx->pairs_ready) return ctx->fail(HFX_ERR_STATE, "hfx_build_K before hfx_build_pairs");
   if (!P || !K || ld < ctx->n_bf) return ctx->fail(HFX_ERR_ARG, "NULL matrix or ld < n_bf");
@@ -412,8 +438,12 @@ extern "C" int hfx_build_K(hfx_ctx* ctx, const double* P, double* K, int ld) {
     L.row_end = ctx->rt.row_base[cp + 1];
     L.bra_bin_start = ctx->rt.bin_start[hi];
     L.ket_bin_start = ctx->rt.bin_start[lo];
-    L.q_begin = ctx->cls_qbegin[cp];
-    L.q_count = ctx->cls_q[cp];
+    // partition `part` of n_parts: a contiguous 1/n_parts of every class's quartet list
+    int64_t p0 = 0, p1 = 0;
+    hfx_part_range(ctx->cls_q[cp], part, n_parts, &p0, &p1);
+    if (p1 == p0) continue;
+    L.q_begin = ctx->cls_qbegin[cp] + p0;
+    L.q_count = p1 - p0;
     L.counters = ctx->timing ? ctx->d_counters + kNCnt * cp : nullptr;
     // mixed precision: classes allowed FP32 run warp groups, so the FP32/FP64 choice per
     // quartet is uniform over the lanes that work on it; the others keep the FP64 kernels

@@ -159,6 +159,11 @@ def load_library(path: str = LIB_PATH):
     L.hfx_energy_noalloc.restype = ctypes.c_int
     L.hfx_measure_fma_peak.argtypes = [dp, dp]
     L.hfx_measure_fma_peak.restype = ctypes.c_int
+    L.hfx_build_K_part.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.hfx_build_K_part.restype = ctypes.c_int
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.hfx_part_range.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, i64p, i64p]
+    L.hfx_part_range.restype = ctypes.c_int
     L.hfx_device_bytes.argtypes = [vp]
     L.hfx_device_bytes.restype = ctypes.c_int64
     u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -200,6 +205,15 @@ def _dp(a):
 
 def _ip(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def part_range(count, part, n_parts):
+    """[q0, q1) of a list of `count` items owned by partition `part` of n_parts (C library)."""
+    q0, q1 = ctypes.c_int64(), ctypes.c_int64()
+    rc = load_library().hfx_part_range(int(count), int(part), int(n_parts), ctypes.byref(q0), ctypes.byref(q1))
+    if rc != 0:
+        raise HFXError(rc, "invalid partition")
+    return q0.value, q1.value
 
 
 def default_options() -> Options:
@@ -274,8 +288,9 @@ class HFX:
     def set_timing(self, on=True):
         self._check(self.L.hfx_set_timing(self.h, 1 if on else 0))
 
-    def build_K(self, P, K=None):
-        """K for the density P (torch float64 CUDA tensor, n x n, contiguous rows)."""
+    def build_K(self, P, K=None, part=0, n_parts=1):
+        """K for the density P (torch float64 CUDA tensor, n x n, contiguous rows); with
+        n_parts > 1 only partition `part` of the quartet list (the parts sum to K)."""
         torch = self.torch
         n = self.n_bf
         if not (P.is_cuda and P.dtype == torch.float64 and P.shape == (n, n) and P.stride(1) == 1):
@@ -285,7 +300,11 @@ class HFX:
         ld = P.stride(0)
         if K.stride(0) != ld or K.stride(1) != 1:
             raise ValueError("K must have the same row stride as P")
-        self._check(self.L.hfx_build_K(self.h, ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(K.data_ptr()), ld))
+        if n_parts == 1:
+            self._check(self.L.hfx_build_K(self.h, ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(K.data_ptr()), ld))
+        else:
+            self._check(self.L.hfx_build_K_part(self.h, ctypes.c_void_p(P.data_ptr()),
+                                                ctypes.c_void_p(K.data_ptr()), ld, int(part), int(n_parts)))
         return K
 
     def build_K_host(self, P: np.ndarray) -> np.ndarray:

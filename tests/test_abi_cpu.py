@@ -82,3 +82,26 @@ def test_tables_regenerate_identically():
     inc = os.path.join(ROOT, "paper_2009_03559_gb300", "csrc", "eri_tables.inc")
     out = subprocess.run([sys.executable, gen], check=True, capture_output=True, text=True).stdout
     assert out == open(inc).read()
+
+
+def test_server_options_and_null_arguments_rejected_on_host(lib):
+    """Server entry points check their arguments before any CUDA call."""
+    import ctypes
+    from paper_2009_03559_gb300 import hfx
+    L = hfx.load_library()
+    o = hfx.ServerOptions()
+    L.hfx_server_default_options(ctypes.byref(o))
+    assert (o.hbm_budget_gb, o.max_inflight, o.max_batch, o.precision) == (120.0, 4, 16, 0)
+    h = ctypes.c_void_p()
+    for field, bad in (("hbm_budget_gb", 0.0), ("max_inflight", 0), ("max_batch", 0), ("precision", 7)):
+        b = hfx.ServerOptions()
+        L.hfx_server_default_options(ctypes.byref(b))
+        setattr(b, field, bad)
+        assert L.hfx_server_create(ctypes.byref(h), ctypes.byref(b)) == -1
+    t = ctypes.c_uint64()
+    r = hfx.Result()
+    assert L.hfx_serve_submit(None, 0, None, None, None, ctypes.byref(t)) == -1
+    assert L.hfx_serve_poll(None, 1, ctypes.byref(r)) == -1
+    assert L.hfx_serve_wait(None, 1, ctypes.c_double(0.0), ctypes.byref(r)) == -1
+    assert L.hfx_serve_drain(None, ctypes.c_double(0.0)) == -1
+    assert L.hfx_server_add_system(None, None, None) == -1

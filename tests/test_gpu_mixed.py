@@ -78,3 +78,20 @@ def test_mixed_diamond64_full_size(hfx_mod):
     print(f"diamond64 mixed: |dE| {abs(e - g['E_K']):.2e} max|dK| over sampled blocks {worst:.2e}")
     assert worst <= TOL
     assert abs(e - g["E_K"]) <= TOL
+
+
+@pytest.mark.parametrize("case", ["cluster16", "diamond16"])
+def test_mixed_global_pmax(hfx_mod, case):
+    """The FP32 test with the whole-matrix max|P| instead of the quartet's four blocks:
+    never more FP32 quartets than the per-quartet test, and within the same tolerance."""
+    s, P = {"cluster16": inputs.config0, "diamond16": lambda: inputs.config1(16)}[case]()
+    m = (1 << 21) - 1
+    hq, Kq, eq = build(hfx_mod, s, P, precision=hfx_mod.HFX_MIXED, fp32_class_mask=m)
+    hg, Kg, eg = build(hfx_mod, s, P, precision=hfx_mod.HFX_MIXED, fp32_class_mask=m, fp32_pmax_global=True)
+    Ko, eo = oracle_K(s, P)
+    nq = sum(hq.stats()["quartets_fp32_class"])
+    ng = sum(hg.stats()["quartets_fp32_class"])
+    print(f"{case}: fp32 quartets per-quartet Pmax {nq}, global Pmax {ng}; "
+          f"max|dK| {np.abs(Kg - Ko).max():.2e} |dE| {abs(eg - eo):.2e}")
+    assert 0 < ng <= nq
+    assert np.abs(Kg - Ko).max() <= TOL and abs(eg - eo) <= TOL

@@ -212,3 +212,22 @@ def test_diamond64_full_size(hfx_mod):
         blk = K[off[I]:off[I] + nb[I], off[J]:off[J] + nb[J]]
         assert np.abs(blk - np.array(b["K"])).max() <= TOL_K
     assert np.array_equal(K, K.T)
+
+
+@pytest.mark.parametrize("n_parts", [2, 3])
+def test_partitions_sum_to_K(hfx_mod, n_parts):
+    """The sharded form (one contiguous 1/G of every class's quartet list per GPU, no
+    communication until one sum of the partial K): the G parts, built one after another on
+    this GPU, add up to the unsplit K and E_K."""
+    s, P = inputs.config1(8)
+    h = hfx_mod.HFX(s).build_pairs()
+    Pd = torch.from_numpy(P).cuda()
+    K = h.build_K(Pd).clone()
+    e = h.energy()
+    acc = torch.zeros_like(K)
+    e_sum = 0.0
+    for r in range(n_parts):
+        acc += h.build_K(Pd, part=r, n_parts=n_parts)
+        e_sum += h.energy()
+    assert torch.abs(acc - K).max().item() <= 1e-12
+    assert abs(e_sum - e) <= 1e-12
