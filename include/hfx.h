@@ -56,6 +56,14 @@ extern "C" {
 #define HFX_FP64 0                /* every integral in FP64 */
 #define HFX_MIXED 1               /* FP32 recurrences for small-bound quartets, see hfx_options */
 
+/* Default classes allowed FP32 recurrences under HFX_MIXED: (pp|ps), (pp|pp), (ds|pp),
+ * (ds|ds), (dp|ps), (dp|pp), (dp|ds), (dp|dp), (dd|ss), (dd|ps), (dd|pp), (dd|ds), (dd|dp).
+ * Left in FP64: the seven classes whose FP64 kernel runs one quartet per thread (FP32 runs
+ * one quartet per warp and was slower there), and (dd|dd), the highest recurrence
+ * (L = 8): on the 64-atom diamond its FP32 recurrences alone moved E_K by 1.1e-7, while
+ * each other class moved it by at most 2e-9. */
+#define HFX_FP32_CLASSES_DEFAULT 0xFFB30
+
 /* work schedules inside a class launch (paper Sec. 3.2, Algorithms 2 and 3) */
 #define HFX_SCHED_QUARTET 0       /* static even split of the screened quartet list */
 #define HFX_SCHED_PAIR 1          /* static even split of the bra pair list, screening after */
@@ -78,8 +86,7 @@ typedef struct {
   int skip_zero_p;     /* 1 (default): skip quartets whose four density blocks P_bd, P_bc,
                           P_ad, P_ac are all exactly zero (their contribution is exactly 0) */
   int fp32_class_mask; /* HFX_MIXED: bit c allows FP32 for quartet class c (index as in
-                          n_quartets_class); default 0x3F = the six classes without d shells
-                          (recurrences of d classes stay FP64) */
+                          n_quartets_class); default HFX_FP32_CLASSES_DEFAULT */
   int fp32_pmax_global;/* HFX_MIXED: 0 (default): Pmax = max(|P_bd|,|P_bc|,|P_ad|,|P_ac|), the
                           largest density element the quartet's four K updates multiply;
                           1: Pmax = max |P| over the whole matrix (more conservative) */
@@ -249,8 +256,8 @@ int hfx_build_K_batched(hfx_ctx* const* ctxs, const double* const* P_dev, double
  * pair lists and Boys table live on the device for the server's life.  A request names
  * a system and gives a density P and a destination for K.  The server keeps a FIFO
  * queue and up to max_inflight steps on the device at once, each on a stream of its
- * own.  Whenever a step slot is free, all queued requests that fit (at most max_batch,
- * in arrival order, while the memory budget allows) form one step: their P are copied
+ * own.  Whenever a step slot is free, the queued requests that fit (in arrival order, at
+ * most max_batch and max_step_quartets, while the memory budget allows) form one step: their P are copied
  * to server-owned device buffers, one batched launch per class evaluates all their
  * quartets (as hfx_batch_run), and each K goes to its destination.  Requests arriving
  * while steps run are admitted as soon as a slot and memory free up, so their work
@@ -269,6 +276,10 @@ typedef struct hfx_server hfx_server;
 
 typedef struct {
   double hbm_budget_gb;  /* device memory the server may hold (default 120 GB) */
+  double max_step_quartets; /* a step takes further queued requests only while its screened
+                            quartets stay within this (default 1e7; a larger request runs
+                            alone): small systems are batched, large ones do not wait for
+                            each other */
   int max_inflight;      /* steps on the device at once, each on its own stream (default 4) */
   int max_batch;         /* most requests in one step (default 16) */
   int precision;         /* HFX_FP64 (default) or HFX_MIXED for every request; the FP32 test

@@ -43,9 +43,7 @@ extern "C" void hfx_default_options(hfx_options* opt) {
   opt->schedule = HFX_SCHED_DYNAMIC;
   opt->skip_zero_p = 1;
   opt->fp32_tau = 1e-6;
-  // s,p classes only: with fp32_tau = 1e-6, FP32 recurrences in d classes moved E_K of
-  // the 64-atom diamond by 1.2e-7, above the 1e-7 tolerance of this path
-  opt->fp32_class_mask = 0x3F;
+  opt->fp32_class_mask = HFX_FP32_CLASSES_DEFAULT;
 }
 
 extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int n_shells,

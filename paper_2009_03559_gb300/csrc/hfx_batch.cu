@@ -37,6 +37,7 @@ int class_hi(int cp) {
 struct BatchWork {
   int cap = 0, n = 0, n_sm = 0;
   bool mixed = false, pmax = false;
+  bool fp32_class[21] = {};  // some system may run this class with FP32 recurrences
   long long total[21] = {};
   int g32[21] = {}, chunk[21] = {};
   EriLaunch *d_launch = nullptr, *h_launch = nullptr;
@@ -81,7 +82,7 @@ cudaError_t bw_alloc(BatchWork& w, int cap, int n_sm) {
 // the default per-class choices: warp groups where a class needs them (or FP32 may be used)
 void bw_default_choices(BatchWork& w) {
   for (int cp = 0; cp < 21; ++cp) {
-    w.g32[cp] = (w.mixed || eri_group_size(cp) == 32) ? 1 : 0;
+    w.g32[cp] = (w.fp32_class[cp] || eri_group_size(cp) == 32) ? 1 : 0;
     w.chunk[cp] = w.g32[cp] ? 8 : 256;
   }
 }
@@ -91,9 +92,14 @@ void bw_default_choices(BatchWork& w) {
 void bw_fill(BatchWork& w, hfx_ctx* const* ctxs, int n, double* const* pmax, double* const* pglob,
              double* const* energy, bool mixed) {
   w.n = n;
-  w.mixed = mixed;
   w.pmax = false;
   for (int s = 0; s < n; ++s) w.pmax = w.pmax || mixed || ctxs[s]->opt.skip_zero_p;
+  w.mixed = false;
+  for (int cp = 0; cp < 21; ++cp) {
+    w.fp32_class[cp] = false;
+    for (int s = 0; s < n; ++s) w.fp32_class[cp] = w.fp32_class[cp] || (mixed && ((ctxs[s]->opt.fp32_class_mask >> cp) & 1));
+    w.mixed = w.mixed || w.fp32_class[cp];
+  }
   for (int cp = 0; cp < 21; ++cp) {
     long long acc = 0;
     long long* seg = w.h_seg + (size_t)cp * (w.cap + 1);
@@ -177,7 +183,7 @@ int bw_grid(const BatchWork& w, int cp, long long items) {
   const int gs = w.g32[cp] ? 32 : 1;
   const long long groups_per_block = eri_block_size() / gs;
   const long long need = (items + groups_per_block - 1) / groups_per_block;
-  const long long cap = (long long)eri_blocks_per_sm(cp, 0, w.g32[cp], w.mixed && w.g32[cp], true) * w.n_sm;
+  const long long cap = (long long)eri_blocks_per_sm(cp, 0, w.g32[cp], w.fp32_class[cp] && w.g32[cp], true) * w.n_sm;
   return (int)std::max(1LL, std::min(need, cap));
 }
 
@@ -201,7 +207,7 @@ cudaError_t bw_enqueue(const BatchWork& w, cudaStream_t s) {
   for (int cp = 0; cp < 21; ++cp) {
     if (w.total[cp] == 0) continue;
     const EriLaunch L = bw_class_launch(w, cp);
-    if ((e = eri_launch(L, cp, 0, bw_grid(w, cp, w.total[cp]), s, w.g32[cp], w.mixed && w.g32[cp], true)) !=
+    if ((e = eri_launch(L, cp, 0, bw_grid(w, cp, w.total[cp]), s, w.g32[cp], w.fp32_class[cp] && w.g32[cp], true)) !=
         cudaSuccess)
       return e;
   }
@@ -378,7 +384,7 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
       EriLaunch L = bw_class_launch(w, cp);
       L.q_count = w1;
       CKB(cudaEventRecord(t0, s));
-      CKB(eri_launch(L, cp, 0, bw_grid(w, cp, w1 - w0), s, w.g32[cp], w.mixed && w.g32[cp], true));
+      CKB(eri_launch(L, cp, 0, bw_grid(w, cp, w1 - w0), s, w.g32[cp], w.fp32_class[cp] && w.g32[cp], true));
       CKB(cudaEventRecord(t1, s));
       CKB(cudaEventSynchronize(t1));
       CKB(cudaEventElapsedTime(&ms, t0, t1));
@@ -393,7 +399,7 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
     struct Cand { int g32, chunk; };
     std::vector<Cand> cands;
     for (int c : {4, 8, 16, 32}) cands.push_back({1, c});
-    if (!w.mixed && eri_group_size(cp) == 1)
+    if (!w.fp32_class[cp] && eri_group_size(cp) == 1)
       for (int c : {128, 256, 512, 1024}) cands.push_back({0, c});
     // window size: grow from 16k quartets until a default-candidate launch takes the target
     long long win = std::min(total, 16384LL);
@@ -527,6 +533,7 @@ extern "C" void hfx_server_default_options(hfx_server_options* opt) {
   if (!opt) return;
   std::memset(opt, 0, sizeof(*opt));
   opt->hbm_budget_gb = 120.0;
+  opt->max_step_quartets = 1e7;
   opt->max_inflight = 4;
   opt->max_batch = 16;
   opt->precision = HFX_FP64;
@@ -557,7 +564,7 @@ extern "C" int hfx_server_create(hfx_server** out, const hfx_server_options* opt
   hfx_server_options o;
   hfx_server_default_options(&o);
   if (opt) o = *opt;
-  if (!(o.hbm_budget_gb > 0.0) || o.max_inflight < 1 || o.max_inflight > 64 || o.max_batch < 1 ||
+  if (!(o.hbm_budget_gb > 0.0) || !(o.max_step_quartets >= 0.0) || o.max_inflight < 1 || o.max_inflight > 64 || o.max_batch < 1 ||
       o.max_batch > 1024 || (o.precision != HFX_FP64 && o.precision != HFX_MIXED)) {
     hfx::set_global_error("hfx_server_create: invalid options");
     return HFX_ERR_ARG;
@@ -581,6 +588,12 @@ extern "C" int hfx_server_create(hfx_server** out, const hfx_server_options* opt
     uint64_t keep = srv->budget;
     e = cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
+  // Memory freed at the end of a step on one slot's stream must not be handed to a step on
+  // another slot by making that stream wait for the first: that would chain the slots.
+  // Reuse only what is known to be free (stream order or completed events).
+  int no = 0;
+  if (e == cudaSuccess) e = cudaMemPoolSetAttribute(srv->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+  if (e == cudaSuccess) e = cudaMemPoolSetAttribute(srv->pool, cudaMemPoolReuseAllowOpportunistic, &no);
   srv->slots.resize(o.max_inflight);
   for (Slot& sl : srv->slots) {
     if (e != cudaSuccess) break;
@@ -685,9 +698,13 @@ static int server_launch_step(hfx_server* srv, Slot& sl, bool* started) {
   *started = false;
   std::vector<uint64_t> take;
   size_t add = 0;
+  double step_q = 0.0;
   while (!srv->queue.empty() && (int)take.size() < srv->opt.max_batch) {
     const Request& r = srv->reqs[srv->queue.front()];
     if (srv->bytes_resident + srv->bytes_requests + add + r.bytes > srv->budget) break;  // FIFO: wait
+    const double q = (double)srv->sys_quartets[r.sys];
+    if (!take.empty() && step_q + q > srv->opt.max_step_quartets) break;
+    step_q += q;
     add += r.bytes;
     take.push_back(srv->queue.front());
     srv->queue.pop_front();

@@ -14,9 +14,14 @@ const EriClassInfo* class_info_host() { return kClassInfo; }
 // Contracted quartet, G = 1: the thread owns the quartet.  Group scratch slots are
 // interleaved over the block's threads (slot k of thread t at smem[k*st + t]).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int contract_g1(const EriLaunch& L, int bra, int ket, double* S, int st) {
-  const EriClassInfo& ci = L.ci;
-  const PairArrays& pa = L.pa;
+// ci is the launch's class record (kernel parameter space); L supplies the system's data.
+// In batched launches L lives in global memory: the fields the primitive loop needs are
+// read into registers once per quartet.
+__device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaunch& L, int bra, int ket, double* S,
+                                           int st) {
+  const PairArrays pa = L.pa;
+  const double omega2 = L.omega2;
+  const double* boys = L.boys;
   double* V = S + ci.work_base * st;
   const int nb = __ldg(pa.prim_n + bra), nk = __ldg(pa.prim_n + ket);
   const PrimPair* pb = pa.prim + __ldg(pa.prim_off + bra);
@@ -29,7 +34,7 @@ __device__ __forceinline__ int contract_g1(const EriLaunch& L, int bra, int ket,
       const PrimPair k = pk[ik];
       CoefRg c;
       double Gm[kMaxLt + 1];
-      if (!prim_setup(b, k, ci.E, ci.F, ci.Lt, L.omega2, L.boys, c, Gm)) continue;
+      if (!prim_setup(b, k, ci.E, ci.F, ci.Lt, omega2, boys, c, Gm)) continue;
       ++any;
       for (int m = 0; m <= ci.Lt; ++m) V[m * st] = Gm[m];
       for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
@@ -81,9 +86,11 @@ __device__ __forceinline__ void post_stages(const EriClassInfo& ci, const PairAr
 }
 
 template <typename R, bool FOLD>
-__device__ __forceinline__ int contract_g32(const EriLaunch& L, int bra, int ket, R* S, R* CF, int lane) {
-  const EriClassInfo& ci = L.ci;
-  const PairArrays& pa = L.pa;
+__device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const EriLaunch& L, int bra, int ket, R* S, R* CF,
+                                            int lane) {
+  const PairArrays pa = L.pa;
+  const double omega2 = L.omega2;
+  const double* boys = L.boys;
   R* V = S + ci.work_base;
   const int nb = __ldg(pa.prim_n + bra), nk = __ldg(pa.prim_n + ket);
   const PrimPair* pb = pa.prim + __ldg(pa.prim_off + bra);
@@ -97,11 +104,11 @@ __device__ __forceinline__ int contract_g32(const EriLaunch& L, int bra, int ket
       const int ib = t / nk, ik = t - ib * nk;
       // the Boys step and the quantities feeding it stay in FP64 in either precision
       if constexpr (sizeof(R) == 4) {
-        prim_setup_f32(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, L.omega2, L.boys, reinterpret_cast<float*>(CF + lane * NCOEF));
+        prim_setup_f32(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, omega2, boys, reinterpret_cast<float*>(CF + lane * NCOEF));
       } else {
         CoefRg c;
         double Gm[kMaxLt + 1];
-        const bool ok = prim_setup(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, L.omega2, L.boys, c, Gm);
+        const bool ok = prim_setup(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, omega2, boys, c, Gm);
         store_coef<R>(c, Gm, ci.Lt, ok, CF + lane * NCOEF);
       }
     }
@@ -159,6 +166,11 @@ __device__ __forceinline__ int contract_g32(const EriLaunch& L, int bra, int ket
 #ifndef HFX_G32_MINB
 #define HFX_G32_MINB 6
 #endif
+// the batched thread-per-quartet kernel carries the batch bookkeeping too: 4 blocks per SM
+// keep it free of spills
+#ifndef HFX_G1B_MINB
+#define HFX_G1B_MINB 4
+#endif
 // the mixed-precision warp kernel carries both recurrence paths: 4 blocks per SM keep it
 // free of spills
 #ifndef HFX_G32M_MINB
@@ -189,21 +201,34 @@ struct Tally {
 };
 
 // Quartets [q0, q1) of the launch record Ls, G = 1: lane `lane` of the warp takes
-// q0 + lane, q0 + lane + 32, ... (neighbouring lanes on neighbouring quartets).
-__device__ __forceinline__ void g1_range(const EriLaunch& Ls, long long q0, long long q1, double* S, int st,
-                                         int lane, Tally& t) {
+// q0 + lane, q0 + lane + 32, ... (neighbouring lanes on neighbouring quartets).  ci: the
+// launch's class record; the system fields used per quartet are copied to registers once
+// per range (Ls may live in global memory, where the K updates could alias it).
+__device__ __forceinline__ void g1_range(const EriClassInfo& ci, const EriLaunch& Ls, long long q0, long long q1,
+                                         double* S, int st, int lane, Tally& t) {
   if (q0 + lane >= q1) return;
-  int r = find_row(Ls.qoff, Ls.row_begin, Ls.row_end, q0 + lane);
+  const long long* qoff = Ls.qoff;
+  const int* sorted = Ls.sorted;
+  const int* psa = Ls.pa.sa;
+  const int* psb = Ls.pa.sb;
+  const int* pn = Ls.pa.prim_n;
+  const int* bf_off = Ls.sh.bf_off;
+  const int row_begin = Ls.row_begin, bra0 = Ls.bra_bin_start, ket0 = Ls.ket_bin_start;
+  const bool skip = Ls.skip_zero;
+  const double* P = Ls.P;
+  double* K = Ls.K;
+  const int ld = Ls.ld;
+  int r = find_row(qoff, row_begin, Ls.row_end, q0 + lane);
   for (long long q = q0 + lane; q < q1; q += 32) {
-    while (__ldg(Ls.qoff + r + 1) <= q) ++r;
-    const int bra_s = Ls.bra_bin_start + (r - Ls.row_begin);
-    const int ket_s = Ls.ket_bin_start + (int)(q - __ldg(Ls.qoff + r));
-    const int bra = __ldg(Ls.sorted + bra_s), ket = __ldg(Ls.sorted + ket_s);
-    const int sa = __ldg(Ls.pa.sa + bra), sb = __ldg(Ls.pa.sb + bra);
-    const int sc = __ldg(Ls.pa.sa + ket), sd = __ldg(Ls.pa.sb + ket);
-    if (Ls.skip_zero && pmax4(Ls, sa, sb, sc, sd) == 0.0) continue;
-    const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
-    const int ne = contract_g1(Ls, bra, ket, S, st);
+    while (__ldg(qoff + r + 1) <= q) ++r;
+    const int bra_s = bra0 + (r - row_begin);
+    const int ket_s = ket0 + (int)(q - __ldg(qoff + r));
+    const int bra = __ldg(sorted + bra_s), ket = __ldg(sorted + ket_s);
+    const int sa = __ldg(psa + bra), sb = __ldg(psb + bra);
+    const int sc = __ldg(psa + ket), sd = __ldg(psb + ket);
+    if (skip && pmax4(Ls, sa, sb, sc, sd) == 0.0) continue;
+    const int npq = __ldg(pn + bra) * __ldg(pn + ket);
+    const int ne = contract_g1(ci, Ls, bra, ket, S, st);
     t.prim += ne;
     t.skip += npq - ne;
     if (!ne) continue;
@@ -212,15 +237,15 @@ __device__ __forceinline__ void g1_range(const EriLaunch& Ls, long long q0, long
     if (sa == sb) deg *= 0.5;
     if (sc == sd) deg *= 0.5;
     if (bra_s == ket_s) deg *= 0.5;
-    digest(Ls.ci, S + Ls.ci.out_base * st, st, __ldg(Ls.sh.bf_off + sa), __ldg(Ls.sh.bf_off + sb),
-           __ldg(Ls.sh.bf_off + sc), __ldg(Ls.sh.bf_off + sd), deg, Ls.P, Ls.K, Ls.ld, 0, 1);
+    digest(ci, S + ci.out_base * st, st, __ldg(bf_off + sa), __ldg(bf_off + sb), __ldg(bf_off + sc),
+           __ldg(bf_off + sd), deg, P, K, ld, 0, 1);
   }
 }
 
 // Quartets [q0, q1) of the launch record Ls, G = 32: the warp takes them one by one.
 template <bool FOLD, bool MIXED>
-__device__ __forceinline__ void g32_range(const EriLaunch& Ls, long long q0, long long q1, double* S, double* CF,
-                                          int lane, Tally& t) {
+__device__ __forceinline__ void g32_range(const EriClassInfo& ci, const EriLaunch& Ls, long long q0, long long q1,
+                                          double* S, double* CF, int lane, Tally& t) {
   float* Sf = reinterpret_cast<float*>(S);  // the FP32 engine reuses the group's memory
   float* CFf = reinterpret_cast<float*>(CF);
   if (q0 >= q1) return;
@@ -245,9 +270,9 @@ __device__ __forceinline__ void g32_range(const EriLaunch& Ls, long long q0, lon
     const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
     int ne;
     if (MIXED && f32)
-      ne = contract_g32<float, FOLD>(Ls, bra, ket, Sf, CFf, lane);
+      ne = contract_g32<float, FOLD>(ci, Ls, bra, ket, Sf, CFf, lane);
     else
-      ne = contract_g32<double, FOLD>(Ls, bra, ket, S, CF, lane);
+      ne = contract_g32<double, FOLD>(ci, Ls, bra, ket, S, CF, lane);
     t.prim += ne;
     t.skip += npq - ne;
     if (!ne) continue;
@@ -263,7 +288,7 @@ __device__ __forceinline__ void g32_range(const EriLaunch& Ls, long long q0, lon
     const int A = __ldg(Ls.sh.bf_off + sa), B = __ldg(Ls.sh.bf_off + sb);
     const int C = __ldg(Ls.sh.bf_off + sc), D = __ldg(Ls.sh.bf_off + sd);
     // an FP32 quartet leaves its final block in FP64 too (see contract_g32)
-    digest(Ls.ci, S + Ls.ci.out_base, 1, A, B, C, D, deg, Ls.P, Ls.K, Ls.ld, lane, 32);
+    digest(ci, S + ci.out_base, 1, A, B, C, D, deg, Ls.P, Ls.K, Ls.ld, lane, 32);
     __syncwarp();
   }
 }
@@ -316,7 +341,7 @@ __device__ __forceinline__ void flush_tally(const EriLaunch& L, const Tally& t) 
 }
 
 template <int MODE, bool BATCH>
-__global__ void __launch_bounds__(64, HFX_G1_MINB) eri_g1_kernel(const EriLaunch L) {
+__global__ void __launch_bounds__(64, BATCH ? HFX_G1B_MINB : HFX_G1_MINB) eri_g1_kernel(const EriLaunch L) {
   extern __shared__ double smem[];
   const int st = blockDim.x;
   double* S = smem + threadIdx.x;
@@ -328,13 +353,15 @@ __global__ void __launch_bounds__(64, HFX_G1_MINB) eri_g1_kernel(const EriLaunch
     const int lane = threadIdx.x & 31;
     Tally t;
     for_each_range<BATCH>(L, gid >> 5, ng >> 5, lane,
-                          [&](const EriLaunch& Ls, long long q0, long long q1) { g1_range(Ls, q0, q1, S, st, lane, t); });
+                          [&](const EriLaunch& Ls, long long q0, long long q1) {
+                            g1_range(L.ci, Ls, q0, q1, S, st, lane, t);
+                          });
     flush_tally(L, t);
   } else {
     for (long long t = gid; t < L.diag_n; t += ng) {
       const int p = __ldg(L.diag_list + t);
       double mx = 0.0;
-      if (contract_g1(L, p, p, S, st)) mx = diag_max(L.ci, S + L.ci.out_base * st, st);
+      if (contract_g1(L.ci, L, p, p, S, st)) mx = diag_max(L.ci, S + L.ci.out_base * st, st);
       L.diag_Q[p] = sqrt(mx);
     }
   }
@@ -356,14 +383,14 @@ __global__ void __launch_bounds__(64, MIXED ? HFX_G32M_MINB : HFX_G32_MINB) eri_
   if (MODE == 0) {
     Tally t;
     for_each_range<BATCH>(L, gid, ng, lane, [&](const EriLaunch& Ls, long long q0, long long q1) {
-      g32_range<FOLD, MIXED>(Ls, q0, q1, S, CF, lane, t);
+      g32_range<FOLD, MIXED>(L.ci, Ls, q0, q1, S, CF, lane, t);
     });
     if (lane == 0) flush_tally(L, t);
   } else {
     for (long long t = gid; t < L.diag_n; t += ng) {
       const int p = __ldg(L.diag_list + t);
       double mx = 0.0;
-      if (contract_g32<double, FOLD>(L, p, p, S, CF, lane)) mx = diag_max(L.ci, S + L.ci.out_base, 1);
+      if (contract_g32<double, FOLD>(L.ci, L, p, p, S, CF, lane)) mx = diag_max(L.ci, S + L.ci.out_base, 1);
       if (lane == 0) L.diag_Q[p] = sqrt(mx);
       __syncwarp();
     }

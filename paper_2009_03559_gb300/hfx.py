@@ -24,6 +24,8 @@ PAIR_CLASSES = ["ss", "ps", "pp", "ds", "dp", "dd"]
 QUARTET_CLASSES = [f"({PAIR_CLASSES[hi]}|{PAIR_CLASSES[lo]})" for hi in range(6) for lo in range(hi + 1)]
 # quartet classes without d shells (bra and ket pair classes among ss, ps, pp)
 SP_CLASS_MASK = sum(1 << (hi * (hi + 1) // 2 + lo) for hi in range(3) for lo in range(hi + 1))
+ALL_CLASS_MASK = (1 << 21) - 1
+FP32_CLASSES_DEFAULT = 0xFFB30  # HFX_FP32_CLASSES_DEFAULT in include/hfx.h
 
 
 class Options(ctypes.Structure):
@@ -34,7 +36,8 @@ class Options(ctypes.Structure):
 
 
 class ServerOptions(ctypes.Structure):
-    _fields_ = [("hbm_budget_gb", ctypes.c_double), ("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int),
+    _fields_ = [("hbm_budget_gb", ctypes.c_double), ("max_step_quartets", ctypes.c_double),
+                ("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
@@ -422,7 +425,8 @@ class Server:
     """Request loop with continuous batching over registered ``HFX`` contexts (the C
     server in hfx_batch.cu; this class only marshals arguments)."""
 
-    def __init__(self, hbm_budget_gb=120.0, max_inflight=4, max_batch=16, precision=HFX_FP64):
+    def __init__(self, hbm_budget_gb=120.0, max_inflight=4, max_batch=16, precision=HFX_FP64,
+                 max_step_quartets=None):
         self.L = load_library()
         o = ServerOptions()
         self.L.hfx_server_default_options(ctypes.byref(o))
@@ -430,6 +434,8 @@ class Server:
         o.max_inflight = int(max_inflight)
         o.max_batch = int(max_batch)
         o.precision = int(precision)
+        if max_step_quartets is not None:
+            o.max_step_quartets = float(max_step_quartets)
         h = ctypes.c_void_p()
         rc = self.L.hfx_server_create(ctypes.byref(h), ctypes.byref(o))
         if rc != 0:

@@ -91,9 +91,10 @@ def test_server_options_and_null_arguments_rejected_on_host(lib):
     L = hfx.load_library()
     o = hfx.ServerOptions()
     L.hfx_server_default_options(ctypes.byref(o))
-    assert (o.hbm_budget_gb, o.max_inflight, o.max_batch, o.precision) == (120.0, 4, 16, 0)
+    assert (o.hbm_budget_gb, o.max_step_quartets, o.max_inflight, o.max_batch, o.precision) == (120.0, 1e7, 4, 16, 0)
     h = ctypes.c_void_p()
-    for field, bad in (("hbm_budget_gb", 0.0), ("max_inflight", 0), ("max_batch", 0), ("precision", 7)):
+    for field, bad in (("hbm_budget_gb", 0.0), ("max_step_quartets", -1.0), ("max_inflight", 0), ("max_batch", 0),
+                       ("precision", 7)):
         b = hfx.ServerOptions()
         L.hfx_server_default_options(ctypes.byref(b))
         setattr(b, field, bad)

@@ -1,7 +1,8 @@
 """Mixed precision: FP32 recurrences for quartets with Q_IJ Q_KL max|P blocks| < 1e-6,
-FP64 Boys step and K accumulation.  Tolerance against the FP64 oracle: max |dK| <= 1e-7
-and |dE_K| <= 1e-7 Hartree (the number the target statement fixes for this path).  Both
-readings of "l >= 2 recurrences stay FP64" are checked: s,p classes only, and all classes."""
+FP64 Boys step, HRR and K accumulation.  Tolerance against the FP64 oracle: max |dK| <=
+1e-7 and |dE_K| <= 1e-7 Hartree (the number the target statement fixes for this path).
+The class masks checked: the default (13 warp-group classes, (dd|dd) kept FP64), s,p
+classes only, and all classes (on the small cases, where it still meets the tolerance)."""
 import json
 import os
 
@@ -38,12 +39,12 @@ def oracle_K(s, P):
     return S.build_K(P, "sym")
 
 
-@pytest.mark.parametrize("mask", ["all", "sp"])
+@pytest.mark.parametrize("mask", ["all", "sp", "default"])
 @pytest.mark.parametrize("case", ["cluster16", "diamond8", "diamond16"])
 def test_mixed_against_oracle(hfx_mod, case, mask):
     s, P = {"cluster16": inputs.config0, "diamond8": lambda: inputs.config1(8),
             "diamond16": lambda: inputs.config1(16)}[case]()
-    m = (1 << 21) - 1 if mask == "all" else hfx_mod.SP_CLASS_MASK
+    m = {"all": hfx_mod.ALL_CLASS_MASK, "sp": hfx_mod.SP_CLASS_MASK, "default": hfx_mod.FP32_CLASSES_DEFAULT}[mask]
     h, K, e = build(hfx_mod, s, P, precision=hfx_mod.HFX_MIXED, fp32_class_mask=m)
     Ko, eo = oracle_K(s, P)
     st = h.stats()

@@ -65,8 +65,9 @@ def run_alone(hfx, systems, reqs, **kw):
 def test_alone_equals_mix(hfx_mod, precision):
     systems = make_systems()
     reqs = request_list(systems)
-    alone = run_alone(hfx_mod, systems, reqs, max_inflight=2, max_batch=4, precision=precision)
-    srv = hfx_mod.Server(max_inflight=2, max_batch=4, precision=precision)
+    kw = dict(max_inflight=2, max_batch=4, precision=precision, max_step_quartets=1e12)
+    alone = run_alone(hfx_mod, systems, reqs, **kw)
+    srv = hfx_mod.Server(**kw)
     ctxs = [hfx_mod.HFX(s, precision=precision).build_pairs() for s in systems]
     ids = [srv.add_system(c) for c in ctxs]
     Ps = [torch.from_numpy(density(systems[i], seed)).cuda() for i, seed in reqs]
@@ -168,3 +169,16 @@ def test_wait_timeout_then_completion(hfx_mod):
     assert srv.poll(t)["status"] in (1, 2)
     r = srv.wait(t)
     assert r["status"] == 0 and np.isfinite(r["energy"])
+
+
+def test_step_quartet_limit(hfx_mod):
+    """With a step limit below every system's quartet count, each step holds one request."""
+    s = inputs.make_system("cluster", 8, seed=9500)
+    srv = hfx_mod.Server(max_inflight=1, max_batch=16, max_step_quartets=1.0)
+    c = hfx_mod.HFX(s).build_pairs()
+    sid = srv.add_system(c)
+    Ps = [torch.from_numpy(density(s, 60 + k)).cuda() for k in range(4)]
+    Ks = [torch.empty_like(P) for P in Ps]
+    res = [srv.wait(t) for t in [srv.submit(sid, P, K) for P, K in zip(Ps, Ks)]]
+    assert all(r["status"] == 0 and r["step_size"] == 1 for r in res)
+    assert srv.stats()["max_step_size"] == 1
