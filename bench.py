@@ -19,6 +19,9 @@ Other workloads (one JSON line each, rank 0, one GPU; reports beside the main li
                          autotuned build replayed from a CUDA graph, vs the same systems
                          built one by one (plain FP64)
   --workload diamond216  216-atom diamond (2808 functions): plain FP64 vs mixed precision
+  --workload balance     the 64-atom build under the three work distributions (static bra-pair
+                         split, Algorithm 2; static quartet split, Algorithm 3; dynamic
+                         chunks): build time and the spread of busy time over the SMs
   --workload serve       request stream (Poisson arrivals, systems from a seeded pool)
                          through the continuous-batching server (mixed precision) vs the
                          same stream built one request at a time (plain FP64, FIFO)
@@ -40,6 +43,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "HFX K-build ms & screened ERI quartets/s vs plain FP64; p50/p99 latency"
+# DRAM bytes (read + write) per launch of the warp-group ERI kernel on the 64-atom workload:
+# ncu dram__bytes_read.sum + dram__bytes_write.sum over its 48 class launches of four builds
+# (814.26 MB), taken on the kernel version with class data read from launch parameters.
+G32_DRAM_BYTES_PER_LAUNCH = 814.26e6 / 48
 MASK_DESC = {"default": "13 classes with warp-group kernels, not (dd|dd)", "sp": "s,p classes only",
              "all": "all classes"}
 
@@ -222,18 +229,23 @@ def run_batch32(args, torch, hfx, inputs):
     seq_ms = a.elapsed_time(b)
     e_seq = [c.energy() for c in ctxs]
     bt = hfx.Batch(ctxs)
-    t0 = time.perf_counter()
-    bt.tune(Ps, Ks)
-    tune_s = time.perf_counter() - t0
-    torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
     a.record()
-    bt.run(Ps, Ks)  # graph capture and instantiation (host) + first launch
+    bt.run(Ps, Ks)  # default per-class choices; graph capture and instantiation + first launch
+    b.record()
+    torch.cuda.synchronize()
+    def_ms = a.elapsed_time(b)
+    t0 = time.perf_counter()
+    bt.tune(Ps, Ks)
+    tune_s = time.perf_counter() - t0
+    a.record()
+    bt.run(Ps, Ks)  # tuned choices: new graph
     b.record()
     torch.cuda.synchronize()
     ck = clocks.stop()
-    bat_ms = a.elapsed_time(b)
+    tuned_ms = a.elapsed_time(b)
+    bat_ms = def_ms  # the configured (default) choices; the tuned run is reported beside it
     e_bat = [c.energy() for c in ctxs]
     dk = max(torch.abs(x - y).max().item() for x, y in zip(Ks, Ks1))
     st = bt.stats()
@@ -246,6 +258,7 @@ def run_batch32(args, torch, hfx, inputs):
                                "seeded coin; plain FP64",
                    "quartets": nq, "systems": [[s.kind, s.n_atoms, s.n_bf] for s, P in systems]},
         "one_by_one": {"ms": seq_ms, "quartets_per_s": nq / (seq_ms * 1e-3)},
+        "batched_default_ms": def_ms, "batched_tuned_ms": tuned_ms,
         "speedup_vs_one_by_one": seq_ms / bat_ms,
         "tuner": {"seconds": tune_s, "group_size_class": st["group_size_class"], "chunk_class": st["chunk_class"],
                   "window_class": st["tune_window_class"]},
@@ -294,6 +307,36 @@ def run_diamond216(args, torch, hfx, inputs):
         "higher_is_better": True, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": workload_desc(s, True, "default"), "quartets": n_q, "fp32_tau": args.fp32_tau},
         "runs": out}), flush=True)
+
+
+def run_balance(args, torch, hfx, inputs):
+    """Load balance of the three distributions of a class launch's quartets over the SMs
+    (the paper's pair vs quartet comparison, plus the dynamic counter): per schedule the
+    K-build time and the per-SM busy time (sum of CTA lifetimes per SM, globaltimer)."""
+    s, P_np = inputs.config1(args.atoms)
+    P = torch.from_numpy(P_np).cuda()
+    out = {}
+    Kref = None
+    for name, sch in (("pair_static", hfx.HFX_SCHED_PAIR), ("quartet_static", hfx.HFX_SCHED_QUARTET),
+                      ("dynamic", hfx.HFX_SCHED_DYNAMIC)):
+        h = hfx.HFX(s, schedule=sch).build_pairs()
+        K = h.build_K(P)  # warm-up
+        h.set_timing(True)
+        h.build_K(P, K)
+        st = h.stats()
+        busy = h.sm_busy_ns()
+        busy = busy[busy > 0]
+        out[name] = {"ms": st["ms_build"], "sm_busy_mean_ms": float(busy.mean()) / 1e6,
+                     "sm_busy_max_ms": float(busy.max()) / 1e6, "sm_busy_min_ms": float(busy.min()) / 1e6,
+                     "imbalance_max_over_mean": float(busy.max() / busy.mean()),
+                     "efficiency_mean_over_max": float(busy.mean() / busy.max()), "sms": int(busy.size)}
+        if Kref is None:
+            Kref = K.clone()
+        out[name]["max_abs_dK_vs_pair_static"] = torch.abs(K - Kref).max().item()
+        h.close()
+    print(json.dumps({"metric": METRIC, "workload": "balance", "value": out["dynamic"]["ms"], "unit": "ms",
+                      "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": workload_desc(s)}, "schedules": out}), flush=True)
 
 
 def run_serve(args, torch, hfx, inputs):
@@ -378,7 +421,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-sample", type=int, default=2000000,
                     help="quartets per oracle step (--impl reference) and for the CPU baseline")
-    ap.add_argument("--workload", default="diamond64", choices=["diamond64", "batch32", "diamond216", "serve"])
+    ap.add_argument("--workload", default="diamond64", choices=["diamond64", "batch32", "diamond216", "serve", "balance"])
     ap.add_argument("--requests", type=int, default=64, help="serve: requests of the stream to run")
     ap.add_argument("--serve-max-atoms", type=int, default=64, help="serve: largest system of the pool")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -410,7 +453,8 @@ def main():
 
     if args.workload != "diamond64":
         if rank == 0:
-            {"batch32": run_batch32, "diamond216": run_diamond216, "serve": run_serve}[args.workload](
+            {"batch32": run_batch32, "diamond216": run_diamond216, "serve": run_serve,
+             "balance": run_balance}[args.workload](
                 args, torch, hfx, inputs)
         if pg:
             pg.destroy_process_group()
@@ -501,7 +545,9 @@ def main():
             "roofline": {"bound": "alu", "kernel": "eri_g32_kernel (classes with warp groups), "
                                                    "CUDA events around each class launch over the timed steps",
                          "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / fp64_peak) if achieved else None,
+                         "traffic": G32_DRAM_BYTES_PER_LAUNCH if (args.atoms == 64 and not mixed) else None,
+                         "traffic_unit": "bytes per launch (ncu dram read + write)",
                          "peak_source": "FP64 FMA-chain probe of this run (hfx_measure_fma_peak)"},
             "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"]},
             "fp64_flops_per_step": st_timed["flops_fp64"],

@@ -226,9 +226,10 @@ typedef struct {
 int hfx_batch_create(hfx_batch** out, hfx_ctx* const* ctxs, int n, void* stream);
 
 /* Autotuner: for every class, times its batched launch with each candidate group size
- * (1 or 32 lanes per quartet, where the class allows both) and dynamic chunk size, and
- * keeps the fastest.  Uses P/K like hfx_batch_run (their K contents are overwritten by
- * the tuning launches; run hfx_batch_run afterwards).  Synchronises. */
+ * (1 or 32 lanes per quartet, where the class allows both) and dynamic chunk size on one
+ * window of the class's quartets, and keeps the fastest; a candidate must beat the current
+ * choice by 5% to replace it.  Uses P/K like hfx_batch_run (their K contents are
+ * overwritten by the tuning launches; run hfx_batch_run afterwards).  Synchronises. */
 int hfx_batch_tune(hfx_batch* b, const double* const* P_dev, double* const* K_dev, const int* ld);
 
 /* Builds K_s for P_s of every system s (device pointers; ld[s] >= n_bf of system s; ld

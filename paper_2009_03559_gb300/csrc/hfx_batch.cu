@@ -401,8 +401,16 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
     for (int c : {4, 8, 16, 32}) cands.push_back({1, c});
     if (!w.fp32_class[cp] && eri_group_size(cp) == 1)
       for (int c : {128, 256, 512, 1024}) cands.push_back({0, c});
-    // window size: grow from 16k quartets until a default-candidate launch takes the target
-    long long win = std::min(total, 16384LL);
+    // window size: grow from 16k quartets until a default-candidate launch takes the target,
+    // and at least two claims for every resident warp of every candidate, so that a large
+    // chunk is not judged on a window that leaves most of the GPU idle
+    long long fill = 0;
+    for (const Cand& cd : cands) {
+      const long long warps = (long long)eri_blocks_per_sm(cp, 0, cd.g32, w.fp32_class[cp] && cd.g32, true) *
+                              w.n_sm * (eri_block_size() / 32);
+      fill = std::max(fill, 2 * warps * cd.chunk);
+    }
+    long long win = std::min(total, std::max(16384LL, fill));
     for (int it = 0; it < 4 && win < total && rc == HFX_OK; ++it) {
       float ms = 0.f;
       const long long w0 = (total - win) / 2;
@@ -412,15 +420,20 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
       win = std::min(total, (long long)(win * std::min(64.0, std::max(2.0, grow))));
     }
     const long long w0 = (total - win) / 2;
-    double best = 1e30;
+    // the current choice is the incumbent; a candidate must beat it by 5% to replace it
+    // (a window is one sample of the class: small gains on it did not carry to whole runs)
     Cand bc = {w.g32[cp], w.chunk[cp]};
+    float inc = 0.f;
+    if ((rc = time_window(cp, w0, w0 + win, &inc)) != HFX_OK) break;
+    double best = inc;
     for (const Cand& cd : cands) {
       if (rc != HFX_OK) break;
+      if (cd.g32 == bc.g32 && cd.chunk == bc.chunk) continue;
       w.g32[cp] = cd.g32;
       w.chunk[cp] = cd.chunk;
       float ms = 0.f;
       if ((rc = time_window(cp, w0, w0 + win, &ms)) != HFX_OK) break;
-      if (ms < best) {
+      if (ms < best && ms < 0.95 * inc) {
         best = ms;
         bc = cd;
       }
