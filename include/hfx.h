@@ -107,7 +107,7 @@ typedef struct {
   double flops_fp64;           /* FP64 flops of the last timed K build (operation-count model
                                   of the kernels: add/mul = 1, fma = 2) */
   double flops_class[21];      /* the same per class */
-  int32_t group_size_class[21];/* lanes per quartet of each class kernel (1 or 32) */
+  int32_t group_size_class[21];/* lanes per quartet of each class in the last build (1 or 32) */
   double ms_pairs;             /* GPU time of the last hfx_build_pairs */
   double ms_build;             /* GPU time of the last hfx_build_K (zero K .. E_K ready) */
   double ms_class[21];         /* GPU time of each class launch in the last K build */
@@ -173,6 +173,12 @@ int hfx_energy(hfx_ctx* ctx, double* out);
 /* Synchronises the stream and fills *out (timings need HFX timing enabled, see
  * hfx_set_timing). */
 int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out);
+
+/* Lanes per quartet for class cls (0..20) in later K builds of this context: 1 (a thread
+ * owns a quartet), 32 (a warp), 0 = the library's default.  Mixed-precision classes always
+ * run 32; 1 needs a class whose scratch fits the thread kernel (the classes that default to
+ * 1), else the build fails with HFX_ERR_CUDA.  Errors: HFX_ERR_ARG. */
+int hfx_set_group_size(hfx_ctx* ctx, int cls, int gs);
 
 /* Enables (1) or disables (0) per-class CUDA-event timing of K builds. */
 int hfx_set_timing(hfx_ctx* ctx, int enable);

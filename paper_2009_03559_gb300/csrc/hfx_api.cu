@@ -189,12 +189,11 @@ EriLaunch hfx::base_launch(hfx_ctx* ctx) {
   return L;
 }
 
-static int grid_for(hfx_ctx* ctx, int cls, int mode, long long work_items, bool g32, bool mixed = false,
+static int grid_for(hfx_ctx* ctx, int cls, int mode, long long work_items, int gs, bool mixed = false,
                     bool batch = false) {
-  const int gs = g32 ? 32 : 1;
-  const int groups_per_block = eri_block_size() / gs;
+  const int groups_per_block = eri_groups_per_block(mode, gs, mixed);
   long long need = (work_items + groups_per_block - 1) / groups_per_block;
-  long long cap = (long long)eri_blocks_per_sm(cls, mode, g32, mixed, batch) * ctx->n_sm;
+  long long cap = (long long)eri_blocks_per_sm(cls, mode, gs, mixed, batch) * ctx->n_sm;
   long long g = std::min(need, cap);
   return (int)std::max(1LL, g);
 }
@@ -283,8 +282,8 @@ extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
         L.diag_list = d_cidx + start;
         L.diag_n = cnt[pc];
         L.diag_Q = ctx->d_Q;
-        const bool g32 = eri_group_size(cls) == 32;
-        CK(eri_launch(L, cls, 1, grid_for(ctx, cls, 1, cnt[pc], g32), s, g32, false, false));
+        const int gs = eri_group_size(cls);
+        CK(eri_launch(L, cls, 1, grid_for(ctx, cls, 1, cnt[pc], gs), s, gs, false, false));
       }
       start += cnt[pc];
     }
@@ -448,11 +447,13 @@ static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int pa
     L.fp32_ok = mixed && ((ctx->opt.fp32_class_mask >> cp) & 1);
     const bool force32 = L.fp32_ok;
     L.work = ctx->d_work + cp;
-    const bool g32 = force32 || eri_group_size(cp) == 32;
-    L.chunk = g32 ? 8 : 256;
+    int gs = ctx->gs_override[cp] ? ctx->gs_override[cp] : eri_group_size(cp);
+    if (force32) gs = 32;
+    ctx->gs_used[cp] = gs;
+    L.chunk = gs == 1 ? 256 : 8;
     const long long items = ctx->opt.schedule == HFX_SCHED_PAIR ? (L.row_end - L.row_begin) : L.q_count;
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[2 + 2 * cp], s));
-    CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items, g32, force32), s, g32, force32, false));
+    CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items, gs, force32), s, gs, force32, false));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3 + 2 * cp], s));
     ctx->class_launched[cp] = true;
   }
@@ -483,6 +484,14 @@ extern "C" int hfx_energy(hfx_ctx* ctx, double* out) {
   return HFX_OK;
 }
 
+extern "C" int hfx_set_group_size(hfx_ctx* ctx, int cls, int gs) {
+  if (!ctx) return HFX_ERR_ARG;
+  if (cls < 0 || cls >= 21 || (gs != 0 && !eri_group_size_valid(gs)))
+    return ctx->fail(HFX_ERR_ARG, "class must be 0..20 and group size 0, 1, 8, 16 or 32");
+  ctx->gs_override[cls] = gs;
+  return HFX_OK;
+}
+
 extern "C" int hfx_set_timing(hfx_ctx* ctx, int enable) {
   if (!ctx) return HFX_ERR_ARG;
   ctx->timing = enable != 0;
@@ -493,7 +502,8 @@ extern "C" int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out) {
   if (!ctx || !out) return HFX_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
   hfx_stats& st = ctx->stats;
-  for (int cp = 0; cp < 21; ++cp) st.group_size_class[cp] = eri_group_size(cp);
+  for (int cp = 0; cp < 21; ++cp)
+    st.group_size_class[cp] = ctx->gs_used[cp] ? ctx->gs_used[cp] : eri_group_size(cp);
   CK(cudaMemcpy(&st.energy, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost));
   if (ctx->timing) {
     float ms = 0.f;

@@ -39,7 +39,7 @@ struct BatchWork {
   bool mixed = false, pmax = false;
   bool fp32_class[21] = {};  // some system may run this class with FP32 recurrences
   long long total[21] = {};
-  int g32[21] = {}, chunk[21] = {};
+  int gs[21] = {}, chunk[21] = {};  // lanes per quartet and dynamic chunk per class
   EriLaunch *d_launch = nullptr, *h_launch = nullptr;
   BatchSys *d_sys = nullptr, *h_sys = nullptr;
   long long *d_seg = nullptr, *h_seg = nullptr;
@@ -82,8 +82,8 @@ cudaError_t bw_alloc(BatchWork& w, int cap, int n_sm) {
 // the default per-class choices: warp groups where a class needs them (or FP32 may be used)
 void bw_default_choices(BatchWork& w) {
   for (int cp = 0; cp < 21; ++cp) {
-    w.g32[cp] = (w.fp32_class[cp] || eri_group_size(cp) == 32) ? 1 : 0;
-    w.chunk[cp] = w.g32[cp] ? 8 : 256;
+    w.gs[cp] = w.fp32_class[cp] ? 32 : eri_group_size(cp);
+    w.chunk[cp] = w.gs[cp] == 1 ? 256 : 8;
   }
 }
 
@@ -180,10 +180,10 @@ EriLaunch bw_class_launch(const BatchWork& w, int cp) {
 }
 
 int bw_grid(const BatchWork& w, int cp, long long items) {
-  const int gs = w.g32[cp] ? 32 : 1;
-  const long long groups_per_block = eri_block_size() / gs;
+  const bool mixed = w.fp32_class[cp] && w.gs[cp] > 1;
+  const long long groups_per_block = eri_groups_per_block(0, w.gs[cp], mixed);
   const long long need = (items + groups_per_block - 1) / groups_per_block;
-  const long long cap = (long long)eri_blocks_per_sm(cp, 0, w.g32[cp], w.fp32_class[cp] && w.g32[cp], true) * w.n_sm;
+  const long long cap = (long long)eri_blocks_per_sm(cp, 0, w.gs[cp], mixed, true) * w.n_sm;
   return (int)std::max(1LL, std::min(need, cap));
 }
 
@@ -207,7 +207,7 @@ cudaError_t bw_enqueue(const BatchWork& w, cudaStream_t s) {
   for (int cp = 0; cp < 21; ++cp) {
     if (w.total[cp] == 0) continue;
     const EriLaunch L = bw_class_launch(w, cp);
-    if ((e = eri_launch(L, cp, 0, bw_grid(w, cp, w.total[cp]), s, w.g32[cp], w.fp32_class[cp] && w.g32[cp], true)) !=
+    if ((e = eri_launch(L, cp, 0, bw_grid(w, cp, w.total[cp]), s, w.gs[cp], w.fp32_class[cp] && w.gs[cp] > 1, true)) !=
         cudaSuccess)
       return e;
   }
@@ -384,7 +384,7 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
       EriLaunch L = bw_class_launch(w, cp);
       L.q_count = w1;
       CKB(cudaEventRecord(t0, s));
-      CKB(eri_launch(L, cp, 0, bw_grid(w, cp, w1 - w0), s, w.g32[cp], w.fp32_class[cp] && w.g32[cp], true));
+      CKB(eri_launch(L, cp, 0, bw_grid(w, cp, w1 - w0), s, w.gs[cp], w.fp32_class[cp] && w.gs[cp] > 1, true));
       CKB(cudaEventRecord(t1, s));
       CKB(cudaEventSynchronize(t1));
       CKB(cudaEventElapsedTime(&ms, t0, t1));
@@ -396,19 +396,20 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
   for (int cp = 0; cp < 21 && rc == HFX_OK; ++cp) {
     const long long total = w.total[cp];
     if (total == 0) continue;
-    struct Cand { int g32, chunk; };
+    struct Cand { int gs, chunk; };
     std::vector<Cand> cands;
-    for (int c : {4, 8, 16, 32}) cands.push_back({1, c});
+    for (int c : {4, 8, 16, 32}) cands.push_back({32, c});
     if (!w.fp32_class[cp] && eri_group_size(cp) == 1)
-      for (int c : {128, 256, 512, 1024}) cands.push_back({0, c});
+      for (int c : {128, 256, 512, 1024}) cands.push_back({1, c});
     // window size: grow from 16k quartets until a default-candidate launch takes the target,
     // and at least two claims for every resident warp of every candidate, so that a large
     // chunk is not judged on a window that leaves most of the GPU idle
     long long fill = 0;
     for (const Cand& cd : cands) {
-      const long long warps = (long long)eri_blocks_per_sm(cp, 0, cd.g32, w.fp32_class[cp] && cd.g32, true) *
-                              w.n_sm * (eri_block_size() / 32);
-      fill = std::max(fill, 2 * warps * cd.chunk);
+      const bool mx = w.fp32_class[cp] && cd.gs > 1;
+      const long long groups = (long long)eri_blocks_per_sm(cp, 0, cd.gs, mx, true) * w.n_sm *
+                               (cd.gs == 1 ? eri_block_size() / 32 : eri_groups_per_block(0, cd.gs, mx));
+      fill = std::max(fill, 2 * groups * cd.chunk);
     }
     long long win = std::min(total, std::max(16384LL, fill));
     for (int it = 0; it < 4 && win < total && rc == HFX_OK; ++it) {
@@ -422,14 +423,14 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
     const long long w0 = (total - win) / 2;
     // the current choice is the incumbent; a candidate must beat it by 5% to replace it
     // (a window is one sample of the class: small gains on it did not carry to whole runs)
-    Cand bc = {w.g32[cp], w.chunk[cp]};
+    Cand bc = {w.gs[cp], w.chunk[cp]};
     float inc = 0.f;
     if ((rc = time_window(cp, w0, w0 + win, &inc)) != HFX_OK) break;
     double best = inc;
     for (const Cand& cd : cands) {
       if (rc != HFX_OK) break;
-      if (cd.g32 == bc.g32 && cd.chunk == bc.chunk) continue;
-      w.g32[cp] = cd.g32;
+      if (cd.gs == bc.gs && cd.chunk == bc.chunk) continue;
+      w.gs[cp] = cd.gs;
       w.chunk[cp] = cd.chunk;
       float ms = 0.f;
       if ((rc = time_window(cp, w0, w0 + win, &ms)) != HFX_OK) break;
@@ -438,7 +439,7 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
         bc = cd;
       }
     }
-    w.g32[cp] = bc.g32;
+    w.gs[cp] = bc.gs;
     w.chunk[cp] = bc.chunk;
     b->tune_ms[cp] = best * (double)total / (double)win;  // projected to the whole class
     b->tune_window[cp] = win;
@@ -457,7 +458,7 @@ extern "C" int hfx_batch_get_stats(hfx_batch* b, hfx_batch_stats* out) {
   std::memset(out, 0, sizeof(*out));
   for (int cp = 0; cp < 21; ++cp) {
     out->n_quartets += b->w.total[cp];
-    out->group_size_class[cp] = b->w.g32[cp] ? 32 : 1;
+    out->group_size_class[cp] = b->w.gs[cp];
     out->chunk_class[cp] = b->w.chunk[cp];
     out->tune_ms_class[cp] = b->tune_ms[cp];
     out->tune_window_class[cp] = b->tune_window[cp];

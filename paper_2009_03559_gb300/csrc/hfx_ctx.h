@@ -42,6 +42,8 @@ struct hfx_ctx {
   cudaEvent_t ev[2 * 21 + 4] = {};
   bool ev_ok = false;
   bool class_launched[21] = {};
+  int gs_override[21] = {};  // lanes per quartet chosen by the caller per class (0 = default)
+  int gs_used[21] = {};      // lanes per quartet of each class in the last build
   hfx_stats stats{};
   float ms_pairs = 0.f;
   std::vector<void*> allocs;       // owned for the context lifetime

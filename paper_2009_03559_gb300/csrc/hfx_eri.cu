@@ -65,14 +65,15 @@ __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaun
 }
 
 // ---------------------------------------------------------------------------
-// Contracted quartet, G = 32: a warp owns the quartet.  Lanes set up 32 primitive
-// quartets at a time (coefficient sets in shared memory), then share the ops of each
-// recurrence level.
+// Contracted quartet, G = GS (8, 16 or 32 lanes of one warp, gm = their lane mask): the
+// group owns the quartet.  Lanes set up GS primitive quartets at a time (coefficient sets
+// in shared memory), then share the ops of each recurrence level.  Smaller groups keep
+// more lanes busy in classes whose recurrence levels have few ops.
 // ---------------------------------------------------------------------------
 // HRR and Cartesian -> spherical stages on the group scratch S (lanes share each stage)
-template <typename R>
+template <typename R, int GS>
 __device__ __forceinline__ void post_stages(const EriClassInfo& ci, const PairArrays& pa, int bra, int ket, R* S,
-                                            int lane) {
+                                            int lane, unsigned gm) {
   R AB[3], CD[3];
   for (int i = 0; i < 3; ++i) {
     AB[i] = R(__ldg(pa.AB + 3 * bra + i));
@@ -80,14 +81,14 @@ __device__ __forceinline__ void post_stages(const EriClassInfo& ci, const PairAr
   }
   for (int s = 0; s < ci.n_post; ++s) {
     const int off = ci.post_off[s], n = ci.post_n[s], type = ci.post_type[s];
-    for (int o = lane; o < n; o += 32) post_op<R>(ld_op(kPostOps, off + o), type, S, 1, AB, CD);
-    __syncwarp();
+    for (int o = lane; o < n; o += GS) post_op<R>(ld_op(kPostOps, off + o), type, S, 1, AB, CD);
+    __syncwarp(gm);
   }
 }
 
-template <typename R, bool FOLD>
+template <typename R, bool FOLD, int GS>
 __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const EriLaunch& L, int bra, int ket, R* S, R* CF,
-                                            int lane) {
+                                            int lane, unsigned gm) {
   const PairArrays pa = L.pa;
   const double omega2 = L.omega2;
   const double* boys = L.boys;
@@ -95,10 +96,10 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const EriLau
   const int nb = __ldg(pa.prim_n + bra), nk = __ldg(pa.prim_n + ket);
   const PrimPair* pb = pa.prim + __ldg(pa.prim_off + bra);
   const PrimPair* pk = pa.prim + __ldg(pa.prim_off + ket);
-  for (int a = lane; a < ci.n_acc; a += 32) S[a] = R(0);
+  for (int a = lane; a < ci.n_acc; a += GS) S[a] = R(0);
   const int npq = nb * nk;
   int any = 0;
-  for (int base = 0; base < npq; base += 32) {
+  for (int base = 0; base < npq; base += GS) {
     const int t = base + lane;
     if (t < npq) {
       const int ib = t / nk, ik = t - ib * nk;
@@ -112,32 +113,32 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const EriLau
         store_coef<R>(c, Gm, ci.Lt, ok, CF + lane * NCOEF);
       }
     }
-    __syncwarp();
-    const int nchunk = min(32, npq - base);
+    __syncwarp(gm);
+    const int nchunk = min(GS, npq - base);
     for (int u = 0; u < nchunk; ++u) {
       const R* cf = CF + u * NCOEF;
       if (cf[CF_SKIP] != R(0)) continue;
       ++any;
       const CoefSm<R> c{cf};
-      for (int m = lane; m <= ci.Lt; m += 32) V[m] = cf[CF_G + m];
-      __syncwarp();
+      for (int m = lane; m <= ci.Lt; m += GS) V[m] = cf[CF_G + m];
+      __syncwarp(gm);
       for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
         const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = lane; o < n; o += 32) vrr_bra<FOLD>(ld_op(kVrrOps, off + o), V, S, 1, c);
-        __syncwarp();
+        for (int o = lane; o < n; o += GS) vrr_bra<FOLD>(ld_op(kVrrOps, off + o), V, S, 1, c);
+        __syncwarp(gm);
       }
       for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
         const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = lane; o < n; o += 32) vrr_ket<FOLD>(ld_op(kVrrOps, off + o), V, S, 1, c);
-        __syncwarp();
+        for (int o = lane; o < n; o += GS) vrr_ket<FOLD>(ld_op(kVrrOps, off + o), V, S, 1, c);
+        __syncwarp(gm);
       }
-      for (int a = lane; a < ci.n_accl; a += 32) {
+      for (int a = lane; a < ci.n_accl; a += GS) {
         const uint32_t w = __ldg(kAccSrc + ci.acc_off + a);
         S[w & 0xFFFF] += V[w >> 16];
       }
-      __syncwarp();
+      __syncwarp(gm);
     }
-    __syncwarp();  // every lane is done with this chunk's coefficient sets
+    __syncwarp(gm);  // every lane is done with this chunk's coefficient sets
   }
   if (!any) return 0;
   if constexpr (sizeof(R) == 4) {
@@ -146,13 +147,13 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const EriLau
     // across distant pairs, run in FP64 on the group's FP64 scratch
     double* Sd = reinterpret_cast<double*>(S);
     double* tmp = reinterpret_cast<double*>(CF);
-    for (int a = lane; a < ci.n_acc; a += 32) tmp[a] = (double)S[a];
-    __syncwarp();
-    for (int a = lane; a < ci.n_acc; a += 32) Sd[a] = tmp[a];
-    __syncwarp();
-    post_stages<double>(ci, pa, bra, ket, Sd, lane);
+    for (int a = lane; a < ci.n_acc; a += GS) tmp[a] = (double)S[a];
+    __syncwarp(gm);
+    for (int a = lane; a < ci.n_acc; a += GS) Sd[a] = tmp[a];
+    __syncwarp(gm);
+    post_stages<double, GS>(ci, pa, bra, ket, Sd, lane, gm);
   } else {
-    post_stages<R>(ci, pa, bra, ket, S, lane);
+    post_stages<R, GS>(ci, pa, bra, ket, S, lane, gm);
   }
   return any;
 }
@@ -243,9 +244,9 @@ __device__ __forceinline__ void g1_range(const EriClassInfo& ci, const EriLaunch
 }
 
 // Quartets [q0, q1) of the launch record Ls, G = 32: the warp takes them one by one.
-template <bool FOLD, bool MIXED>
+template <bool FOLD, bool MIXED, int GS>
 __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const EriLaunch& Ls, long long q0, long long q1,
-                                          double* S, double* CF, int lane, Tally& t) {
+                                          double* S, double* CF, int lane, unsigned gm, Tally& t) {
   float* Sf = reinterpret_cast<float*>(S);  // the FP32 engine reuses the group's memory
   float* CFf = reinterpret_cast<float*>(CF);
   if (q0 >= q1) return;
@@ -270,9 +271,9 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const EriLaunc
     const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
     int ne;
     if (MIXED && f32)
-      ne = contract_g32<float, FOLD>(ci, Ls, bra, ket, Sf, CFf, lane);
+      ne = contract_g32<float, FOLD, GS>(ci, Ls, bra, ket, Sf, CFf, lane, gm);
     else
-      ne = contract_g32<double, FOLD>(ci, Ls, bra, ket, S, CF, lane);
+      ne = contract_g32<double, FOLD, GS>(ci, Ls, bra, ket, S, CF, lane, gm);
     t.prim += ne;
     t.skip += npq - ne;
     if (!ne) continue;
@@ -288,8 +289,8 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const EriLaunc
     const int A = __ldg(Ls.sh.bf_off + sa), B = __ldg(Ls.sh.bf_off + sb);
     const int C = __ldg(Ls.sh.bf_off + sc), D = __ldg(Ls.sh.bf_off + sd);
     // an FP32 quartet leaves its final block in FP64 too (see contract_g32)
-    digest(ci, S + ci.out_base, 1, A, B, C, D, deg, Ls.P, Ls.K, Ls.ld, lane, 32);
-    __syncwarp();
+    digest(ci, S + ci.out_base, 1, A, B, C, D, deg, Ls.P, Ls.K, Ls.ld, lane, GS);
+    __syncwarp(gm);
   }
 }
 
@@ -297,8 +298,9 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const EriLaunc
 // Dynamic: chunks claimed from the launch's device counter.  Batched (L.n_sys > 0): chunks
 // of the systems' concatenated quartet lists; a chunk is split at system boundaries
 // (L.seg[s] = first index of system s) and each part runs with that system's record.
-template <bool BATCH, class F>
-__device__ __forceinline__ void for_each_range(const EriLaunch& L, long long wid, long long nw, int lane, F&& f) {
+template <bool BATCH, int GS, class F>
+__device__ __forceinline__ void for_each_range(const EriLaunch& L, long long wid, long long nw, int lane, unsigned gm,
+                                               F&& f) {
   if (!BATCH && L.schedule != 2) {
     long long q0, q1;
     group_range(L, wid, nw, q0, q1);
@@ -309,7 +311,7 @@ __device__ __forceinline__ void for_each_range(const EriLaunch& L, long long wid
   while (true) {
     unsigned long long c = 0;
     if (lane == 0) c = atomicAdd(L.work, (unsigned long long)L.chunk);
-    c = __shfl_sync(0xffffffffu, c, 0);
+    c = __shfl_sync(gm, c, 0, GS);
     long long c0 = (long long)c;
     if (c0 >= total) break;
     const long long c1 = min(c0 + L.chunk, total);
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(64, BATCH ? HFX_G1B_MINB : HFX_G1_MINB) eri_g1
   if (MODE == 0) {
     const int lane = threadIdx.x & 31;
     Tally t;
-    for_each_range<BATCH>(L, gid >> 5, ng >> 5, lane,
+    for_each_range<BATCH, 32>(L, gid >> 5, ng >> 5, lane, 0xffffffffu,
                           [&](const EriLaunch& Ls, long long q0, long long q1) {
                             g1_range(L.ci, Ls, q0, q1, S, st, lane, t);
                           });
@@ -368,31 +370,34 @@ __global__ void __launch_bounds__(64, BATCH ? HFX_G1B_MINB : HFX_G1_MINB) eri_g1
   record_busy(L, t0);
 }
 
-template <int MODE, bool FOLD, bool MIXED, bool BATCH>
+template <int MODE, bool FOLD, bool MIXED, bool BATCH, int GS>
 __global__ void __launch_bounds__(64, MIXED ? HFX_G32M_MINB : HFX_G32_MINB) eri_g32_kernel(const EriLaunch L,
                                                                                             int group_stride) {
+  static_assert(GS == 8 || GS == 16 || GS == 32, "group size");
+  static_assert(!MIXED || GS == 32, "the FP32 engine widens its block through 32 coefficient sets");
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gpb = blockDim.x >> 5;
-  double* S = smem + warp * group_stride;
+  const int lane = threadIdx.x & (GS - 1), grp = threadIdx.x / GS;
+  const unsigned gm = GS == 32 ? 0xffffffffu : (((1u << GS) - 1u) << ((threadIdx.x & 31) & ~(GS - 1)));
+  const int gpb = blockDim.x / GS;
+  double* S = smem + grp * group_stride;
   double* CF = S + L.ci.scratch + (L.ci.scratch & 1);
-  const long long gid = (long long)blockIdx.x * gpb + warp;
+  const long long gid = (long long)blockIdx.x * gpb + grp;
   const long long ng = (long long)gridDim.x * gpb;
   unsigned long long t0 = 0;
   if (L.busy && threadIdx.x == 0) t0 = globaltimer_ns();
   if (MODE == 0) {
     Tally t;
-    for_each_range<BATCH>(L, gid, ng, lane, [&](const EriLaunch& Ls, long long q0, long long q1) {
-      g32_range<FOLD, MIXED>(L.ci, Ls, q0, q1, S, CF, lane, t);
+    for_each_range<BATCH, GS>(L, gid, ng, lane, gm, [&](const EriLaunch& Ls, long long q0, long long q1) {
+      g32_range<FOLD, MIXED, GS>(L.ci, Ls, q0, q1, S, CF, lane, gm, t);
     });
     if (lane == 0) flush_tally(L, t);
   } else {
     for (long long t = gid; t < L.diag_n; t += ng) {
       const int p = __ldg(L.diag_list + t);
       double mx = 0.0;
-      if (contract_g32<double, FOLD>(L.ci, L, p, p, S, CF, lane)) mx = diag_max(L.ci, S + L.ci.out_base, 1);
+      if (contract_g32<double, FOLD, GS>(L.ci, L, p, p, S, CF, lane, gm)) mx = diag_max(L.ci, S + L.ci.out_base, 1);
       if (lane == 0) L.diag_Q[p] = sqrt(mx);
-      __syncwarp();
+      __syncwarp(gm);
     }
   }
   record_busy(L, t0);
@@ -408,34 +413,49 @@ int eri_group_size(int cls) {
   return kClassInfo[cls].scratch <= HFX_G1_MAX_SCRATCH ? 1 : 32;
 }
 
-static int g32_stride(int cls) {
+// Groups of 8 or 16 lanes (several quartets per warp) were measured on the 64-atom diamond:
+// 1.1x to 10x slower than whole warps in every warp-group class and slower than one thread
+// per quartet in the others, because each group needs its own scratch and coefficient
+// sets, so shared memory caps the resident warps.  The kernel keeps the group size as a
+// template parameter; only 32 is built.
+bool eri_group_size_valid(int gs) { return gs == 1 || gs == 32; }
+
+static int group_stride(int cls, int gs) {
   const int s = kClassInfo[cls].scratch;
-  return s + (s & 1) + 32 * NCOEF + 1;  // +1: stagger the groups' banks
+  return s + (s & 1) + gs * NCOEF + 1;  // +1: stagger the groups' banks
 }
 
 // classes whose tables fold the accumulation (the thread-per-quartet ones)
 static bool class_folds(int cls) { return kClassInfo[cls].scratch <= HFX_G1_MAX_SCRATCH; }
 
-// The kernel instance for a class launch.  g32: warp groups (forced for mixed precision);
+template <int MODE, bool MIXED, bool BATCH, int GS>
+static const void* group_kernel(bool fold) {
+  return fold ? (const void*)eri_g32_kernel<MODE, true, MIXED, BATCH, GS>
+              : (const void*)eri_g32_kernel<MODE, false, MIXED, BATCH, GS>;
+}
+
+// The kernel instance for a class launch.  gs: lanes per quartet (1 = a thread, 32 = a warp);
 // mode 1 = Schwarz diagonal; batch = quartets of several systems in one launch.
-static const void* kernel_ptr(int cls, int mode, bool g32, bool mixed, bool batch) {
+static const void* kernel_ptr(int cls, int mode, int gs, bool mixed, bool batch) {
   const bool fold = class_folds(cls);
-  if (!g32) {
+  if (gs == 1) {
     if (mode == 1) return (const void*)eri_g1_kernel<1, false>;
     return batch ? (const void*)eri_g1_kernel<0, true> : (const void*)eri_g1_kernel<0, false>;
   }
-  if (mode == 1) return fold ? (const void*)eri_g32_kernel<1, true, false, false> : (const void*)eri_g32_kernel<1, false, false, false>;
-  if (mixed) {
-    if (batch) return fold ? (const void*)eri_g32_kernel<0, true, true, true> : (const void*)eri_g32_kernel<0, false, true, true>;
-    return fold ? (const void*)eri_g32_kernel<0, true, true, false> : (const void*)eri_g32_kernel<0, false, true, false>;
-  }
-  if (batch) return fold ? (const void*)eri_g32_kernel<0, true, false, true> : (const void*)eri_g32_kernel<0, false, false, true>;
-  return fold ? (const void*)eri_g32_kernel<0, true, false, false> : (const void*)eri_g32_kernel<0, false, false, false>;
+  if (mode == 1) return group_kernel<1, false, false, 32>(fold);
+  if (mixed) return batch ? group_kernel<0, true, true, 32>(fold) : group_kernel<0, true, false, 32>(fold);
+  return batch ? group_kernel<0, false, true, 32>(fold) : group_kernel<0, false, false, 32>(fold);
 }
 
-size_t eri_smem_bytes(int cls, bool g32) {
-  if (!g32) return sizeof(double) * (size_t)kClassInfo[cls].scratch * kBlock;
-  return sizeof(double) * (size_t)g32_stride(cls) * (kBlock / 32);
+// the group size a launch actually runs with
+static int effective_gs(int mode, int gs, bool mixed) {
+  if (gs == 1) return 1;
+  return (mode == 1 || mixed || !eri_group_size_valid(gs)) ? 32 : gs;
+}
+
+size_t eri_smem_bytes(int cls, int gs) {
+  if (gs == 1) return sizeof(double) * (size_t)kClassInfo[cls].scratch * kBlock;
+  return sizeof(double) * (size_t)group_stride(cls, gs) * (kBlock / gs);
 }
 
 int eri_block_size() { return kBlock; }
@@ -443,38 +463,42 @@ int eri_block_size() { return kBlock; }
 cudaError_t eri_prepare() {
   // allow the largest dynamic shared memory any class needs, for every instance
   size_t mx = 0;
-  for (int c = 0; c < HFX_N_CLASSES; ++c) {
-    mx = std::max(mx, eri_smem_bytes(c, true));
-    if (eri_group_size(c) == 1) mx = std::max(mx, eri_smem_bytes(c, false));  // only these run G = 1
-  }
+  for (int c = 0; c < HFX_N_CLASSES; ++c)
+    for (int gs : {1, 32}) mx = std::max(mx, eri_smem_bytes(c, gs));
+  if (mx > 227 * 1024) mx = 227 * 1024;
   for (int cls : {0, HFX_N_CLASSES - 1})
     for (int mode = 0; mode < 2; ++mode)
-      for (int g32 = 0; g32 < 2; ++g32)
+      for (int gs : {1, 32})
         for (int mixed = 0; mixed < 2; ++mixed)
           for (int batch = 0; batch < 2; ++batch) {
-            cudaError_t e = cudaFuncSetAttribute(kernel_ptr(cls, mode, g32, mixed, batch),
+            cudaError_t e = cudaFuncSetAttribute(kernel_ptr(cls, mode, gs, mixed, batch),
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
             if (e != cudaSuccess) return e;
           }
   return cudaSuccess;
 }
 
-int eri_blocks_per_sm(int cls, int mode, bool g32, bool mixed, bool batch) {
+int eri_blocks_per_sm(int cls, int mode, int gs, bool mixed, bool batch) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(cls, mode, g32, mixed, batch), kBlock,
-                                                    eri_smem_bytes(cls, g32)) != cudaSuccess)
+  const int g = effective_gs(mode, gs, mixed);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(cls, mode, g, mixed, batch), kBlock,
+                                                    eri_smem_bytes(cls, g)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
-cudaError_t eri_launch(const EriLaunch& L, int cls, int mode, int grid, cudaStream_t stream, bool g32, bool mixed,
+int eri_groups_per_block(int mode, int gs, bool mixed) { return kBlock / effective_gs(mode, gs, mixed); }
+
+cudaError_t eri_launch(const EriLaunch& L, int cls, int mode, int grid, cudaStream_t stream, int gs, bool mixed,
                        bool batch) {
-  const size_t smem = eri_smem_bytes(cls, g32);
-  const void* k = kernel_ptr(cls, mode, g32, mixed, batch);
-  int gs = g32_stride(cls);
+  const int g = effective_gs(mode, gs, mixed);
+  const size_t smem = eri_smem_bytes(cls, g);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  const void* k = kernel_ptr(cls, mode, g, mixed, batch);
+  int stride = group_stride(cls, g);
   void* args_g1[] = {(void*)&L};
-  void* args_g32[] = {(void*)&L, (void*)&gs};
-  return cudaLaunchKernel(k, dim3(grid), dim3(kBlock), g32 ? args_g32 : args_g1, smem, stream);
+  void* args_grp[] = {(void*)&L, (void*)&stride};
+  return cudaLaunchKernel(k, dim3(grid), dim3(kBlock), g == 1 ? args_g1 : args_grp, smem, stream);
 }
 
 }  // namespace hfx

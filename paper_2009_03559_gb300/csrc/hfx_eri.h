@@ -7,15 +7,19 @@ namespace hfx {
 
 struct EriLaunch;
 
-int eri_group_size(int cls);
-size_t eri_smem_bytes(int cls, bool g32);
+// Group sizes (lanes per quartet): 1 (a thread) or 32 (a warp).  Mixed-precision and
+// Schwarz-diagonal launches run groups of 32 whatever gs > 1 is asked.
+int eri_group_size(int cls);  // default for a class: 1 or 32
+bool eri_group_size_valid(int gs);
+size_t eri_smem_bytes(int cls, int gs);
 int eri_block_size();
 cudaError_t eri_prepare();
-int eri_blocks_per_sm(int cls, int mode, bool g32, bool mixed, bool batch);
+int eri_blocks_per_sm(int cls, int mode, int gs, bool mixed, bool batch);
+int eri_groups_per_block(int mode, int gs, bool mixed);
 
 }  // namespace hfx
 
 namespace hfx {
-cudaError_t eri_launch(const EriLaunch& L, int cls, int mode, int grid, cudaStream_t stream, bool g32, bool mixed,
+cudaError_t eri_launch(const EriLaunch& L, int cls, int mode, int grid, cudaStream_t stream, int gs, bool mixed,
                        bool batch);
 }

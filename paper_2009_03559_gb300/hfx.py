@@ -129,6 +129,8 @@ def load_library(path: str = LIB_PATH):
     L.hfx_energy.restype = ctypes.c_int
     L.hfx_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     L.hfx_get_stats.restype = ctypes.c_int
+    L.hfx_set_group_size.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.hfx_set_group_size.restype = ctypes.c_int
     L.hfx_set_timing.argtypes = [vp, ctypes.c_int]
     L.hfx_set_timing.restype = ctypes.c_int
     L.hfx_n_basis.argtypes = [vp]
@@ -287,6 +289,10 @@ class HFX:
         self._check(self.L.hfx_build_pairs(self.h))
         self.pairs_built = True
         return self
+
+    def set_group_size(self, cls, gs):
+        """Lanes per quartet for quartet class cls in later builds (0 = default)."""
+        self._check(self.L.hfx_set_group_size(self.h, int(cls), int(gs)))
 
     def set_timing(self, on=True):
         self._check(self.L.hfx_set_timing(self.h, 1 if on else 0))

@@ -231,3 +231,22 @@ def test_partitions_sum_to_K(hfx_mod, n_parts):
         e_sum += h.energy()
     assert torch.abs(acc - K).max().item() <= 1e-12
     assert abs(e_sum - e) <= 1e-12
+
+
+def test_group_size_override_same_K(hfx_mod):
+    """A class run by a thread per quartet or by a warp per quartet gives the same K."""
+    s, P = inputs.config1(8)
+    h = hfx_mod.HFX(s).build_pairs()
+    Pd = torch.from_numpy(P).cuda()
+    K0 = h.build_K(Pd).clone()
+    st0 = h.stats()["group_size_class"]
+    for c in range(21):
+        if st0[c] == 1:
+            h.set_group_size(c, 32)
+    h.set_group_size(5, 1)  # (pp|pp): warp by default, its scratch fits the thread kernel
+    K1 = h.build_K(Pd)
+    st1 = h.stats()["group_size_class"]
+    assert st1[5] == 1 and all(st1[c] == 32 for c in range(21) if st0[c] == 1)
+    assert torch.abs(K1 - K0).max().item() <= 1e-12
+    with pytest.raises(hfx_mod.HFXError):
+        h.set_group_size(3, 8)
