@@ -194,7 +194,7 @@ def cpu_baseline(args):
     from paper_2009_03559_gb300 import inputs
     s, P = inputs.config1(64)
     S = oracle.Screen(oracle.Basis(s))
-    sample = oracle_sample(S, s, n=args.ref_sample)
+    sample = oracle_sample(S, s, n=args.cpu_sample)
     S.eval_quartets(sample[:2000])
     t0 = time.perf_counter()
     S.eval_quartets(sample)
@@ -416,11 +416,12 @@ def run_serve(args, torch, hfx, inputs):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--ref-sample", type=int, default=2000000,
-                    help="quartets per oracle step (--impl reference) and for the CPU baseline")
+    ap.add_argument("--ref-sample", type=int, default=2000000, help="quartets per oracle step (--impl reference)")
+    ap.add_argument("--cpu-sample", type=int, default=5000000,
+                    help="quartets of the CPU-oracle baseline on the main line (10-30 s of host work)")
     ap.add_argument("--workload", default="diamond64", choices=["diamond64", "batch32", "diamond216", "serve", "balance"])
     ap.add_argument("--requests", type=int, default=64, help="serve: requests of the stream to run")
     ap.add_argument("--serve-max-atoms", type=int, default=64, help="serve: largest system of the pool")
@@ -553,6 +554,10 @@ def main():
             "fp64_flops_per_step": st_timed["flops_fp64"],
             "fp32_flops_per_step": st_timed["flops_fp32"],
             "quartets_evaluated_per_step": sum(st_timed["quartets_evaluated_class"]),
+            # class mixes compare on these: primitive quartets and spherical integrals per second
+            "prim_quartets_per_s": sum(st_timed["prim_quartets_class"]) / (total_ms / args.steps * 1e-3),
+            "sph_integrals_per_s": sum(q * n for q, n in zip(st_timed["n_quartets_class"], hfx.CLASS_SPH_SIZE))
+                                   / (total_ms / args.steps * 1e-3),
             "quartets_fp32_per_step": sum(st_timed["quartets_fp32_class"]),
             "fp64_tflops_step": st_timed["flops_fp64"] / (total_ms / args.steps * 1e-3) / 1e12,
             "fp32_peak_tflops": fp32_peak,
