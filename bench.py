@@ -382,7 +382,7 @@ def run_serve(args, torch, hfx, inputs):
     srv.drain()
     span2 = time.perf_counter() - t0
     ck = clocks.stop()
-    res = [srv.poll(t) for t in tickets]
+    res = [srv.poll(t, release=True) for t in tickets]
     st = srv.stats()
     lat2 = [r["t_done_ms"] - r["t_submit_ms"] for r in res]
     done2 = max(r["t_done_ms"] for r in res) - min(r["t_submit_ms"] for r in res)

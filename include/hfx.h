@@ -348,6 +348,12 @@ int hfx_serve_poll(hfx_server* srv, uint64_t ticket, hfx_result* out);
  * passes (then HFX_ERR_TIMEOUT, with the request still queued or running). */
 int hfx_serve_wait(hfx_server* srv, uint64_t ticket, double timeout_ms, hfx_result* out);
 
+/* Forgets a finished (done or failed) request: its ticket becomes unknown.  The server
+ * keeps every finished request's result until this call, so long-running callers release
+ * each ticket after reading it.  Errors: HFX_ERR_ARG (unknown ticket), HFX_ERR_STATE (still
+ * queued or running). */
+int hfx_serve_release(hfx_server* srv, uint64_t ticket);
+
 /* Retires finished steps and starts new ones; returns the number of requests not done. */
 int hfx_serve_progress(hfx_server* srv);
 

@@ -860,6 +860,19 @@ extern "C" int hfx_serve_poll(hfx_server* srv, uint64_t ticket, hfx_result* out)
   return r;
 }
 
+extern "C" int hfx_serve_release(hfx_server* srv, uint64_t ticket) {
+  if (!srv) return HFX_ERR_ARG;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->reqs.find(ticket);
+  if (it == srv->reqs.end()) return srv->fail(HFX_ERR_ARG, "hfx_serve_release: unknown ticket");
+  Request& r = it->second;
+  if (r.status == HFX_REQ_QUEUED || r.status == HFX_REQ_RUNNING)
+    return srv->fail(HFX_ERR_STATE, "hfx_serve_release: the request is not finished");
+  recycle_event(srv, r);
+  srv->reqs.erase(it);
+  return HFX_OK;
+}
+
 extern "C" int hfx_serve_progress(hfx_server* srv) {
   if (!srv) return HFX_ERR_ARG;
   std::lock_guard<std::mutex> lk(srv->mu);

@@ -22,6 +22,9 @@ REQ_DONE, REQ_QUEUED, REQ_RUNNING = 0, 1, 2
 
 PAIR_CLASSES = ["ss", "ps", "pp", "ds", "dp", "dd"]
 QUARTET_CLASSES = [f"({PAIR_CLASSES[hi]}|{PAIR_CLASSES[lo]})" for hi in range(6) for lo in range(hi + 1)]
+# spherical integrals per quartet of each class: product of (2l+1) over its four shells
+_PAIR_SIZE = [1, 3, 9, 5, 15, 25]  # ss, ps, pp, ds, dp, dd
+CLASS_SPH_SIZE = [_PAIR_SIZE[hi] * _PAIR_SIZE[lo] for hi in range(6) for lo in range(hi + 1)]
 # quartet classes without d shells (bra and ket pair classes among ss, ps, pp)
 SP_CLASS_MASK = sum(1 << (hi * (hi + 1) // 2 + lo) for hi in range(3) for lo in range(hi + 1))
 ALL_CLASS_MASK = (1 << 21) - 1
@@ -184,6 +187,8 @@ def load_library(path: str = LIB_PATH):
     L.hfx_serve_poll.restype = ctypes.c_int
     L.hfx_serve_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(Result)]
     L.hfx_serve_wait.restype = ctypes.c_int
+    L.hfx_serve_release.argtypes = [vp, ctypes.c_uint64]
+    L.hfx_serve_release.restype = ctypes.c_int
     L.hfx_serve_progress.argtypes = [vp]
     L.hfx_serve_progress.restype = ctypes.c_int
     L.hfx_serve_drain.argtypes = [vp, ctypes.c_double]
@@ -474,19 +479,28 @@ class Server:
         self._keep[t.value] = (P, K_out)
         return t.value
 
-    def poll(self, ticket) -> dict:
+    def poll(self, ticket, release=False) -> dict:
+        """State of a request; with release=True a finished request is also forgotten by
+        the server (its ticket becomes unknown)."""
         r = Result()
         self._check(self.L.hfx_serve_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(r)))
         if r.status <= 0:
             self._keep.pop(ticket, None)
+            if release:
+                self.release(ticket)
         return r.as_dict()
 
-    def wait(self, ticket, timeout_ms=-1.0) -> dict:
+    def wait(self, ticket, timeout_ms=-1.0, release=False) -> dict:
         r = Result()
         self._check(self.L.hfx_serve_wait(self.h, ctypes.c_uint64(ticket), ctypes.c_double(timeout_ms),
                                           ctypes.byref(r)))
         self._keep.pop(ticket, None)
+        if release:
+            self.release(ticket)
         return r.as_dict()
+
+    def release(self, ticket):
+        self._check(self.L.hfx_serve_release(self.h, ctypes.c_uint64(ticket)))
 
     def progress(self) -> int:
         return self._check(self.L.hfx_serve_progress(self.h))

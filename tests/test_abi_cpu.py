@@ -106,3 +106,4 @@ def test_server_options_and_null_arguments_rejected_on_host(lib):
     assert L.hfx_serve_wait(None, 1, ctypes.c_double(0.0), ctypes.byref(r)) == -1
     assert L.hfx_serve_drain(None, ctypes.c_double(0.0)) == -1
     assert L.hfx_server_add_system(None, None, None) == -1
+    assert L.hfx_serve_release(None, 1) == -1

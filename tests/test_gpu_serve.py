@@ -167,8 +167,13 @@ def test_wait_timeout_then_completion(hfx_mod):
         srv.wait(t, timeout_ms=0.0)
     assert ei.value.code == -6
     assert srv.poll(t)["status"] in (1, 2)
-    r = srv.wait(t)
+    with pytest.raises(hfx_mod.HFXError) as ei:   # not finished: cannot be released
+        srv.release(t)
+    assert ei.value.code == -5
+    r = srv.wait(t, release=True)
     assert r["status"] == 0 and np.isfinite(r["energy"])
+    with pytest.raises(hfx_mod.HFXError):         # released: the ticket is gone
+        srv.poll(t)
 
 
 def test_step_quartet_limit(hfx_mod):
