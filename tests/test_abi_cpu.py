@@ -107,3 +107,22 @@ def test_server_options_and_null_arguments_rejected_on_host(lib):
     assert L.hfx_serve_drain(None, ctypes.c_double(0.0)) == -1
     assert L.hfx_server_add_system(None, None, None) == -1
     assert L.hfx_serve_release(None, 1) == -1
+
+
+def test_bench_oracle_sample_is_canonical_and_kept():
+    """The CPU-baseline sampler draws kept canonical quartets (I>=J, K>=L, pair IJ at or
+    after pair KL in the kept list, Q_IJ Q_KL >= tau)."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2009_03559_gb300 import inputs
+    s, P = inputs.config1(8)
+    S = oracle.Screen(oracle.Basis(s))
+    smp = bench.oracle_sample(S, s, 3000)
+    Q, cut, kept, qmax = S.export()
+    assert smp.shape == (3000, 4)
+    I, J, K, L = smp.T
+    assert np.all(I >= J) and np.all(K >= L)
+    assert np.all(kept[I, J]) and np.all(kept[K, L])
+    assert np.all(Q[I, J] * Q[K, L] >= S.tau)

@@ -90,3 +90,38 @@ def test_batch_and_requests():
     times = [r[0] for r in reqs]
     assert all(np.diff(times) > 0)
     assert all(16 <= n <= 512 for _, n, _ in systems)
+
+
+def test_request_stream_statistics():
+    """Poisson arrivals at 50/s: mean gap 1/50 s (2000 gaps: within 10 %); pool sizes are
+    log-uniform in [16, 512] (median near sqrt(16*512) = 90.5); both generators occur."""
+    systems, reqs = inputs.config4_requests()
+    gaps = np.diff([0.0] + [t for t, _, _ in reqs])
+    assert abs(gaps.mean() - 1 / 50) < 0.1 / 50
+    assert 0.8 < gaps.std() / gaps.mean() < 1.2           # exponential: cv = 1
+    sizes = np.array([n for _, n, _ in systems])
+    assert 45 < np.median(sizes) < 180
+    assert {k for k, _, _ in systems} == {"cluster", "diamond"}
+    assert all(0 <= w < 64 for _, w, _ in reqs)
+    assert len({sd for _, _, sd in reqs}) == len(reqs)     # a fresh P seed per request
+
+
+def test_scaled_serving_pool_stays_in_range():
+    systems, reqs = inputs.config4_requests(n_requests=64, n_hi=64)
+    assert all(16 <= n <= 64 for _, n, _ in systems)
+    assert len(reqs) == 64
+
+
+def test_batch_of_32_matches_recipe():
+    """32 systems, atom counts in 8..128, kind by coin; seeds 2000 + i; P per kind."""
+    sys_ = inputs.config2_systems()
+    assert len(sys_) == 32
+    kinds = {s.kind for s, _ in sys_}
+    assert kinds == {"cluster", "diamond"}
+    for i, (s, p) in enumerate(sys_):
+        assert s.seed == 2000 + i and 8 <= s.n_atoms <= 128
+        assert np.allclose(p, p.T)
+        if s.kind == "diamond":
+            assert s.rcut == 6.0 and s.tau == 1e-8
+        else:
+            assert s.rcut == 0.0 and s.tau == 1e-10
