@@ -433,6 +433,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--fp32-classes", default="default", choices=["default", "all", "sp"])
     ap.add_argument("--fp32-tau", type=float, default=1e-6)
+    ap.add_argument("--density-tau", type=float, default=0.0,
+                    help="density-weighted screening threshold (0 = off, the benchmark setting)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_info()
@@ -466,7 +468,7 @@ def main():
     mixed = args.precision == "mixed"
     h = hfx.HFX(s, stream=stream, precision=hfx.HFX_MIXED if mixed else hfx.HFX_FP64,
                 fp32_class_mask=class_mask(hfx, args.fp32_classes),
-                fp32_tau=args.fp32_tau)
+                fp32_tau=args.fp32_tau, density_tau=args.density_tau)
     h.build_pairs()
     P = torch.from_numpy(P_np).cuda()
     K = torch.empty_like(P)
@@ -541,7 +543,9 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if not mixed else "f64+f32",
             "data": "synthetic",
-            "config": {"workload": workload_desc(s, mixed, args.fp32_classes), "n_bf": s.n_bf, "quartets_per_step": n_q,
+            "config": {"workload": workload_desc(s, mixed, args.fp32_classes)
+                                   + (f"; density-weighted screening {args.density_tau:g}" if args.density_tau else ""),
+                       "n_bf": s.n_bf, "quartets_per_step": n_q,
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{ws}",
                        "energy_E_K": energy},
             "e2e": {"value": n_q / float(np.median(e2e_t)) if e2e_t else None, "unit": "quartets/s",

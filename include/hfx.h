@@ -90,7 +90,12 @@ typedef struct {
   int fp32_pmax_global;/* HFX_MIXED: 0 (default): Pmax = max(|P_bd|,|P_bc|,|P_ad|,|P_ac|), the
                           largest density element the quartet's four K updates multiply;
                           1: Pmax = max |P| over the whole matrix (more conservative) */
-  int reserved[3];     /* set to 0 */
+  int reserved[1];     /* set to 0 */
+  double density_tau;  /* density-weighted screening (default 0 = off): a quartet is also
+                          dropped when Q_IJ Q_KL max(|P_bd|,|P_bc|,|P_ad|,|P_ac|) <
+                          density_tau; it changes K by at most that bound per dropped quartet
+                          and block element, and extends the exact-zero skip to small
+                          densities (Sec. 3.1 screening with the density folded in) */
 } hfx_options;
 
 typedef struct {

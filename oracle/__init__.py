@@ -91,6 +91,8 @@ def lib():
             L.ora_count_quartets.restype = None
             L.ora_build_K.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int, dp]
             L.ora_build_K.restype = ctypes.c_double
+            L.ora_build_K_dens.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
+            L.ora_build_K_dens.restype = ctypes.c_double
             L.ora_K_block.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int, dp]
             L.ora_K_block.restype = ctypes.c_int
             L.ora_trace_PK.argtypes = [ctypes.c_int, dp, dp]
@@ -221,6 +223,20 @@ class Screen:
         K = np.zeros((n, n))
         ek = lib().ora_build_K(self.h, _dp(P), 0 if mode == "plain" else 1, int(nthreads), _dp(K))
         return K, float(ek)
+
+    def build_K_dens(self, P: np.ndarray, dens_tau: float, mode: str = "sym", nthreads: int = 0):
+        """K and E_K with the density-weighted quartet test added to the keep rule:
+        Q_IJ Q_KL max(|P| over the blocks (J,L), (J,K), (I,L), (I,K)) >= dens_tau.
+        Also returns the block maxima of |P| (n_shells x n_shells)."""
+        n = self.basis.n_bf
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        assert P.shape == (n, n)
+        K = np.zeros((n, n))
+        ns = self.basis.n_shells
+        pm = np.zeros(ns * ns)
+        ek = lib().ora_build_K_dens(self.h, _dp(P), 0 if mode == "plain" else 1, int(nthreads),
+                                    float(dens_tau), _dp(K), _dp(pm))
+        return K, float(ek), pm.reshape(ns, ns)
 
     def K_block(self, P: np.ndarray, I: int, Ks: int) -> np.ndarray:
         P = np.ascontiguousarray(P, dtype=np.float64)

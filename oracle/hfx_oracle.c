@@ -534,6 +534,10 @@ int ora_prim_cart(const int *l4, const double *alpha4, const double *centres12, 
 typedef struct {
   const ora_basis *B;
   double omega, tau, rcut;
+  /* density-weighted screening of one K build (ora_build_K_dens): block maxima of |P|
+   * (n_shells^2) and the threshold; NULL / 0 otherwise */
+  const double *pm;
+  double dens_tau;
   double *Q;        /* n_shells^2, symmetric: sqrt(max |(mu nu|mu nu)|) */
   unsigned char *cut_ok; /* n_shells^2: orbital-cutoff test passed */
   unsigned char *kept;   /* n_shells^2: pair kept for the quartet loops */
@@ -622,7 +626,21 @@ void ora_screen_export(const void *vs, double *Q, unsigned char *cut_ok, unsigne
 static inline int keep4(const ora_screen *s, int I, int J, int K, int L) {
   int n = s->B->n_shells;
   size_t ij = (size_t)I * n + J, kl = (size_t)K * n + L;
-  return s->kept[ij] && s->kept[kl] && s->Q[ij] * s->Q[kl] >= s->tau;
+  if (!(s->kept[ij] && s->kept[kl] && s->Q[ij] * s->Q[kl] >= s->tau)) return 0;
+  if (s->pm) {
+    /* density-weighted test: the quartet's K updates multiply the density blocks
+     * (J,L), (J,K), (I,L), (I,K); drop it when Q_IJ Q_KL times their largest |P| is below
+     * dens_tau (the same value for all eight orderings of the quartet) */
+    double m = s->pm[(size_t)J * n + L];
+    double t = s->pm[(size_t)J * n + K];
+    if (t > m) m = t;
+    t = s->pm[(size_t)I * n + L];
+    if (t > m) m = t;
+    t = s->pm[(size_t)I * n + K];
+    if (t > m) m = t;
+    if (s->Q[ij] * s->Q[kl] * m < s->dens_tau) return 0;
+  }
+  return 1;
 }
 
 /* pair class index of (l1, l2): ss 0, ps 1, pp 2, ds 3, dp 4, dd 5 */
@@ -795,6 +813,35 @@ double ora_build_K(const void *vs, const double *P, int mode, int nthreads, doub
   else
     build_K_sym(s, P, Kout, nthreads);
   return ora_trace_PK(s->B->n_bf, P, Kout);
+}
+
+/* The same K build with the density-weighted quartet test added to the keep rule
+ * (dens_tau > 0): Q_IJ Q_KL max(|P| over the blocks (J,L), (J,K), (I,L), (I,K)) >= dens_tau.
+ * pm_out (n_shells^2, may be NULL) receives the block maxima of |P|. */
+double ora_build_K_dens(void *vs, const double *P, int mode, int nthreads, double dens_tau, double *Kout,
+                        double *pm_out) {
+  ora_screen *s = (ora_screen *)vs;
+  const ora_basis *B = s->B;
+  int n = B->n_shells, nb = B->n_bf;
+  double *pm = (double *)calloc((size_t)n * n > 0 ? (size_t)n * n : 1, sizeof(double));
+  for (int I = 0; I < n; ++I)
+    for (int J = 0; J < n; ++J) {
+      double m = 0.0;
+      for (int a = 0; a < nsph(B->l[I]); ++a)
+        for (int b = 0; b < nsph(B->l[J]); ++b) {
+          double v = fabs(P[(size_t)(B->bf_off[I] + a) * nb + B->bf_off[J] + b]);
+          if (v > m) m = v;
+        }
+      pm[(size_t)I * n + J] = m;
+    }
+  if (pm_out) memcpy(pm_out, pm, sizeof(double) * (size_t)n * n);
+  s->pm = pm;
+  s->dens_tau = dens_tau;
+  double e = ora_build_K(vs, P, mode, nthreads, Kout);
+  s->pm = NULL;
+  s->dens_tau = 0.0;
+  free(pm);
+  return e;
 }
 
 /* One block K_{mu nu}, mu in shell I, nu in shell Ks, by the plain definition (sum over

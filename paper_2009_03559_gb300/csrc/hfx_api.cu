@@ -63,6 +63,7 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
   hfx_default_options(&o);
   if (opt) o = *opt;
   if (!(o.omega >= 0.0) || !(o.schwarz_tau >= 0.0) || !(o.prim_tau >= 0.0) || !(o.fp32_tau >= 0.0) ||
+      !(o.density_tau >= 0.0) ||
       (o.precision != HFX_FP64 && o.precision != HFX_MIXED) ||
       (o.fp32_pmax_global != 0 && o.fp32_pmax_global != 1) ||
       (o.schedule != HFX_SCHED_QUARTET && o.schedule != HFX_SCHED_PAIR && o.schedule != HFX_SCHED_DYNAMIC)) {
@@ -413,7 +414,7 @@ static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int pa
   L.ld = ld;
   if (ctx->opt.schedule == HFX_SCHED_DYNAMIC) CK(cudaMemsetAsync(ctx->d_work, 0, 32 * sizeof(unsigned long long), s));
   const bool mixed = ctx->opt.precision == HFX_MIXED;
-  if (ctx->opt.skip_zero_p || mixed) {
+  if (ctx->opt.skip_zero_p || mixed || ctx->opt.density_tau > 0.0) {
     const bool glob = mixed && ctx->opt.fp32_pmax_global;
     CK(launch_pmax(ctx->n_shells, ctx->d_bf_off, ctx->d_l, P, ld, ctx->d_pmax, glob ? ctx->d_pglob : nullptr, s));
     L.pmax = ctx->d_pmax;
@@ -422,6 +423,7 @@ static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int pa
   }
   L.skip_zero = ctx->opt.skip_zero_p;
   L.fp32_tau = ctx->opt.fp32_tau;
+  L.dens_tau = ctx->opt.density_tau;
   L.Qs = ctx->d_Qs;
   if (ctx->timing) L.busy = ctx->d_busy;
   for (int cp = 0; cp < 21; ++cp) {

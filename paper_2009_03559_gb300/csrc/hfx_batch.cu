@@ -93,7 +93,8 @@ void bw_fill(BatchWork& w, hfx_ctx* const* ctxs, int n, double* const* pmax, dou
              double* const* energy, bool mixed) {
   w.n = n;
   w.pmax = false;
-  for (int s = 0; s < n; ++s) w.pmax = w.pmax || mixed || ctxs[s]->opt.skip_zero_p;
+  for (int s = 0; s < n; ++s)
+    w.pmax = w.pmax || mixed || ctxs[s]->opt.skip_zero_p || ctxs[s]->opt.density_tau > 0.0;
   w.mixed = false;
   for (int cp = 0; cp < 21; ++cp) {
     w.fp32_class[cp] = false;
@@ -131,6 +132,7 @@ void bw_fill(BatchWork& w, hfx_ctx* const* ctxs, int n, double* const* pmax, dou
       L.fp32_ok = mixed && ((c->opt.fp32_class_mask >> cp) & 1);
       L.fp32_tau = c->opt.fp32_tau;
       L.pglob = glob ? pglob[s] : nullptr;
+      L.dens_tau = c->opt.density_tau;
       L.Qs = c->d_Qs;
       w.h_launch[(size_t)cp * w.cap + s] = L;
     }

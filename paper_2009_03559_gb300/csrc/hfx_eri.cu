@@ -216,6 +216,8 @@ __device__ __forceinline__ void g1_range(const EriClassInfo& ci, const EriLaunch
   const int* bf_off = Ls.sh.bf_off;
   const int row_begin = Ls.row_begin, bra0 = Ls.bra_bin_start, ket0 = Ls.ket_bin_start;
   const bool skip = Ls.skip_zero;
+  const double dens = Ls.dens_tau;
+  const double* Qs = Ls.Qs;
   const double* P = Ls.P;
   double* K = Ls.K;
   const int ld = Ls.ld;
@@ -227,7 +229,9 @@ __device__ __forceinline__ void g1_range(const EriClassInfo& ci, const EriLaunch
     const int bra = __ldg(sorted + bra_s), ket = __ldg(sorted + ket_s);
     const int sa = __ldg(psa + bra), sb = __ldg(psb + bra);
     const int sc = __ldg(psa + ket), sd = __ldg(psb + ket);
-    if (skip && pmax4(Ls, sa, sb, sc, sd) == 0.0) continue;
+    const double pm = pmax4(Ls, sa, sb, sc, sd);
+    if (skip && pm == 0.0) continue;
+    if (dens > 0.0 && __ldg(Qs + bra_s) * __ldg(Qs + ket_s) * pm < dens) continue;
     const int npq = __ldg(pn + bra) * __ldg(pn + ket);
     const int ne = contract_g1(ci, Ls, bra, ket, S, st);
     t.prim += ne;
@@ -260,6 +264,8 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const EriLaunc
     const int sc = __ldg(Ls.pa.sa + ket), sd = __ldg(Ls.pa.sb + ket);
     const double pm = pmax4(Ls, sa, sb, sc, sd);
     if (Ls.skip_zero && pm == 0.0) continue;
+    // density-weighted screening (off when dens_tau = 0)
+    if (Ls.dens_tau > 0.0 && __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pm < Ls.dens_tau) continue;
     // mixed precision: FP32 recurrences when the Schwarz bound times the largest density
     // element the quartet touches (or the largest of all of P) is below fp32_tau
     // (warp-uniform decision)

@@ -171,6 +171,7 @@ struct EriLaunch {
   int fp32_ok;                  // mixed precision allowed for this class
   double fp32_tau;              // FP32 iff Q_IJ Q_KL Pmax < fp32_tau, Pmax = max|P_blocks| ...
   const double* pglob;          // ... or, when non-NULL, *pglob = max |P| over the matrix
+  double dens_tau;              // > 0: drop quartets with Q_IJ Q_KL max|P_blocks| < dens_tau
   const double* Qs;             // Schwarz factor of each sorted pair
   // batched launch (n_sys > 0): quartets of all systems' lists for this class, concatenated;
   // seg[s] = first index of system s (seg[n_sys] = total = q_count); batch[s] = that

@@ -35,7 +35,8 @@ class Options(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("schwarz_tau", ctypes.c_double), ("rcut_bohr", ctypes.c_double),
                 ("prim_tau", ctypes.c_double), ("fp32_tau", ctypes.c_double), ("precision", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("skip_zero_p", ctypes.c_int), ("fp32_class_mask", ctypes.c_int),
-                ("fp32_pmax_global", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("fp32_pmax_global", ctypes.c_int), ("reserved", ctypes.c_int * 1),
+                ("density_tau", ctypes.c_double)]
 
 
 class ServerOptions(ctypes.Structure):
@@ -251,7 +252,7 @@ class HFX:
 
     def __init__(self, system, stream=None, tau=None, rcut=None, omega=None, schedule=HFX_SCHED_DYNAMIC,
                  prim_tau=None, skip_zero_p=True, precision=HFX_FP64, fp32_tau=None, fp32_class_mask=None,
-                 fp32_pmax_global=False):
+                 fp32_pmax_global=False, density_tau=0.0):
         import torch  # device memory and streams only
         if not torch.cuda.is_available():
             raise RuntimeError("HFX needs a CUDA device; there is no CPU path")
@@ -273,6 +274,7 @@ class HFX:
         if fp32_class_mask is not None:
             o.fp32_class_mask = fp32_class_mask
         o.fp32_pmax_global = 1 if fp32_pmax_global else 0
+        o.density_tau = float(density_tau)
         self.options = o
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         xyz, sa, sl, sn, al, co = system.basis_arrays()

@@ -250,3 +250,24 @@ def test_group_size_override_same_K(hfx_mod):
     assert torch.abs(K1 - K0).max().item() <= 1e-12
     with pytest.raises(hfx_mod.HFXError):
         h.set_group_size(3, 8)
+
+
+@pytest.mark.parametrize("dens_tau", [1e-7, 1e-4])
+def test_density_weighted_screening(hfx_mod, dens_tau):
+    """Density-weighted screening (quartets with Q_IJ Q_KL max|P blocks| < dens_tau dropped)
+    against the oracle applying the same rule; fewer quartets evaluated than without it."""
+    s, P = inputs.config1(8)
+    h = hfx_mod.HFX(s, density_tau=dens_tau).build_pairs()
+    h.set_timing(True)
+    K = h.build_K(torch.from_numpy(P).cuda()).cpu().numpy()
+    e = h.energy()
+    n_eval = sum(h.stats()["quartets_evaluated_class"])
+    h0 = hfx_mod.HFX(s).build_pairs()
+    h0.set_timing(True)
+    h0.build_K(torch.from_numpy(P).cuda())
+    n_eval0 = sum(h0.stats()["quartets_evaluated_class"])
+    S = oracle.Screen(oracle.Basis(s))
+    Ko, eo, pm = S.build_K_dens(P, dens_tau, "sym")
+    assert np.abs(K - Ko).max() <= TOL_K
+    assert abs(e - eo) <= TOL_E
+    assert n_eval < n_eval0
