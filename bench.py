@@ -45,8 +45,8 @@ sys.path.insert(0, ROOT)
 METRIC = "HFX K-build ms & screened ERI quartets/s vs plain FP64; p50/p99 latency"
 # DRAM bytes (read + write) per launch of the warp-group ERI kernel on the 64-atom workload:
 # ncu dram__bytes_read.sum + dram__bytes_write.sum over its 48 class launches of four builds
-# (814.26 MB), taken on the kernel version with class data read from launch parameters.
-G32_DRAM_BYTES_PER_LAUNCH = 814.26e6 / 48
+# (798.66 MB), taken on the current kernel version (with the density-screening test).
+G32_DRAM_BYTES_PER_LAUNCH = 798.66e6 / 48
 MASK_DESC = {"default": "13 classes with warp-group kernels, not (dd|dd)", "sp": "s,p classes only",
              "all": "all classes"}
 
