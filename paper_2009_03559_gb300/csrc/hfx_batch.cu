@@ -405,7 +405,7 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
       for (int c : {128, 256, 512, 1024}) cands.push_back({1, c});
     // window size: grow from 16k quartets until a default-candidate launch takes the target,
     // and at least two claims for every resident warp of every candidate, so that a large
-    // chunk is not judged on a window that leaves most of the GPU idle
+    // chunk is not timed on a window that leaves most of the GPU idle
     long long fill = 0;
     for (const Cand& cd : cands) {
       const bool mx = w.fp32_class[cp] && cd.gs > 1;

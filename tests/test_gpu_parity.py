@@ -81,7 +81,7 @@ def check_screening(h, S, system):
 
 
 def test_cluster16_full(hfx_mod):
-    """configs[0]: 16-atom s,p cluster, tau 1e-10, no cutoff, full K."""
+    """The 16-atom s,p cluster, tau 1e-10, no cutoff, full K."""
     s, P = inputs.config0()
     h, K, e = gpu_build(hfx_mod, s, P)
     B, S, Ko, eo = oracle_build(s, P)
@@ -194,7 +194,7 @@ def test_bad_angular_momentum_rejected(hfx_mod):
 
 
 def test_diamond64_full_size(hfx_mod):
-    """configs[1] at full size (64 atoms, 832 functions) in the bench's launch setup:
+    """The 64-atom diamond at full size (832 functions) in the bench's launch setup:
     E_K and sampled K blocks against stored oracle values (tests/golden/make_golden.py)."""
     path = os.path.join(GOLD, "oracle_diamond64.json")
     if not os.path.exists(path):
