@@ -709,6 +709,50 @@ static int server_retire(hfx_server* srv) {
   return HFX_OK;
 }
 
+// Enqueues one step for the requests `take` on the slot's stream: server-owned P/K/maxima
+// from the pool, P copied in after the submitter's stream, the batched build, K copied
+// out, memory given back, E_K of every request to the slot's host array, the done event.
+static cudaError_t step_enqueue(hfx_server* srv, Slot& sl, const std::vector<uint64_t>& take) {
+  cudaStream_t s = sl.stream;
+  const int n = (int)take.size();
+  std::vector<hfx_ctx*> ctxs(n);
+  std::vector<const double*> P(n);
+  std::vector<double*> K(n), pmax(n), pglob(n), energy(n);
+  cudaError_t e;
+  if ((e = cudaEventRecord(sl.start, s)) != cudaSuccess) return e;
+  for (int i = 0; i < n; ++i) {
+    Request& r = srv->reqs[take[i]];
+    hfx_ctx* c = srv->systems[r.sys];
+    const size_t nn = (size_t)c->n_bf * c->n_bf;
+    void* m = nullptr;
+    if ((e = cudaMallocFromPoolAsync(&m, r.bytes, srv->pool, s)) != cudaSuccess) return e;
+    r.mem = (char*)m;
+    double* Pd = (double*)r.mem;
+    if ((e = cudaStreamWaitEvent(s, r.ready, 0)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(Pd, r.P_src, nn * sizeof(double), cudaMemcpyDefault, s)) != cudaSuccess) return e;
+    ctxs[i] = c;
+    P[i] = Pd;
+    K[i] = (double*)(r.mem + align_up(nn * sizeof(double)));
+    pmax[i] = (double*)(r.mem + 2 * align_up(nn * sizeof(double)));
+    pglob[i] = (double*)(r.mem + r.bytes - 256);
+    energy[i] = sl.d_energy + i;
+  }
+  bw_fill(sl.w, ctxs.data(), n, pmax.data(), pglob.data(), energy.data(), srv->opt.precision == HFX_MIXED);
+  bw_default_choices(sl.w);
+  bw_set_buffers(sl.w, P.data(), K.data(), nullptr);
+  if ((e = bw_enqueue(sl.w, s)) != cudaSuccess) return e;
+  for (int i = 0; i < n; ++i) {
+    Request& r = srv->reqs[take[i]];
+    const size_t nn = (size_t)ctxs[i]->n_bf * ctxs[i]->n_bf;
+    if ((e = cudaMemcpyAsync(r.K_dst, K[i], nn * sizeof(double), cudaMemcpyDefault, s)) != cudaSuccess) return e;
+    if ((e = cudaFreeAsync(r.mem, s)) != cudaSuccess) return e;
+    r.mem = nullptr;  // given back in stream order
+  }
+  if ((e = cudaMemcpyAsync(sl.h_energy, sl.d_energy, sizeof(double) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  return cudaEventRecord(sl.done, s);
+}
+
 // Starts one step on a free slot with the queued requests that fit; false if none started.
 static int server_launch_step(hfx_server* srv, Slot& sl, bool* started) {
   *started = false;
@@ -726,48 +770,27 @@ static int server_launch_step(hfx_server* srv, Slot& sl, bool* started) {
     srv->queue.pop_front();
   }
   if (take.empty()) return HFX_OK;
-  cudaStream_t s = sl.stream;
-  const int n = (int)take.size();
-  std::vector<hfx_ctx*> ctxs(n);
-  std::vector<const double*> P(n);
-  std::vector<double*> K(n), pmax(n), pglob(n), energy(n);
   const double now = host_ms_since(srv->t0);
-  CKS(cudaEventRecord(sl.start, s));
-  for (int i = 0; i < n; ++i) {
-    Request& r = srv->reqs[take[i]];
-    hfx_ctx* c = srv->systems[r.sys];
-    const size_t nn = (size_t)c->n_bf * c->n_bf;
-    void* m = nullptr;
-    CKS(cudaMallocFromPoolAsync(&m, r.bytes, srv->pool, s));
-    r.mem = (char*)m;
-    double* Pd = (double*)r.mem;
-    double* Kd = (double*)(r.mem + align_up(nn * sizeof(double)));
-    double* pm = (double*)(r.mem + 2 * align_up(nn * sizeof(double)));
-    double* pg = (double*)(r.mem + r.bytes - 256);
-    CKS(cudaStreamWaitEvent(s, r.ready, 0));
-    CKS(cudaMemcpyAsync(Pd, r.P_src, nn * sizeof(double), cudaMemcpyDefault, s));
-    ctxs[i] = c;
-    P[i] = Pd;
-    K[i] = Kd;
-    pmax[i] = pm;
-    pglob[i] = pg;
-    energy[i] = sl.d_energy + i;
+  const cudaError_t e = step_enqueue(srv, sl, take);
+  if (e != cudaSuccess) {
+    // the step's requests fail (their waits return); memory already taken is given back
+    for (uint64_t t : take) {
+      Request& r = srv->reqs[t];
+      if (r.mem) cudaFreeAsync(r.mem, sl.stream);
+      r.mem = nullptr;
+      r.status = HFX_ERR_CUDA;
+      srv->st.n_failed++;
+    }
+    cudaGetLastError();
+    return srv->fail(HFX_ERR_CUDA, std::string("server step launch failed: ") + cudaGetErrorString(e));
+  }
+  for (uint64_t t : take) {
+    Request& r = srv->reqs[t];
     r.status = HFX_REQ_RUNNING;
-    r.step_size = n;
+    r.step_size = (int)take.size();
     r.t_admit = now;
   }
-  bw_fill(sl.w, ctxs.data(), n, pmax.data(), pglob.data(), energy.data(), srv->opt.precision == HFX_MIXED);
-  bw_default_choices(sl.w);
-  bw_set_buffers(sl.w, P.data(), K.data(), nullptr);
-  CKS(bw_enqueue(sl.w, s));
-  for (int i = 0; i < n; ++i) {
-    Request& r = srv->reqs[take[i]];
-    const size_t nn = (size_t)ctxs[i]->n_bf * ctxs[i]->n_bf;
-    CKS(cudaMemcpyAsync(r.K_dst, K[i], nn * sizeof(double), cudaMemcpyDefault, s));
-    CKS(cudaFreeAsync(r.mem, s));
-  }
-  CKS(cudaMemcpyAsync(sl.h_energy, sl.d_energy, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-  CKS(cudaEventRecord(sl.done, s));
+  const int n = (int)take.size();
   sl.reqs = take;
   sl.busy = true;
   srv->bytes_requests += add;
