@@ -126,3 +126,22 @@ def test_bench_oracle_sample_is_canonical_and_kept():
     assert np.all(I >= J) and np.all(K >= L)
     assert np.all(kept[I, J]) and np.all(kept[K, L])
     assert np.all(Q[I, J] * Q[K, L] >= S.tau)
+
+
+def test_header_compiles_as_c_and_host_calls_work(lib, tmp_path):
+    """include/hfx.h is plain C: a C99 program using it compiles with warnings as errors,
+    links against the library and its host-side calls answer without a GPU."""
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2009_03559_gb300 import hfx
+    libdir = os.path.dirname(hfx.LIB_PATH)
+    exe = str(tmp_path / "abi_from_c")
+    src = os.path.join(ROOT, "tests", "c", "abi_from_c.c")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), src,
+                        "-o", exe, "-L", libdir, "-lhfx", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert "C ABI ok" in r.stdout
