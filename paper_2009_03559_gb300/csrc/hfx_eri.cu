@@ -1,6 +1,7 @@
 // ERI kernels: one class launch evaluates every screened quartet of one class pair
-// (bra pair bin >= ket pair bin) and digests it into the half exchange matrix, or, in
-// diagonal mode, evaluates (p|p) for candidate pairs and stores the Schwarz factor.
+// (bra pair bin >= ket pair bin) -- of one system, or of all systems of a batch -- and
+// digests it into the half exchange matrix, or, in diagonal mode, evaluates (p|p) for
+// candidate pairs and stores the Schwarz factor.
 #include <algorithm>
 #include <cstdio>
 #include "eri_engine.cuh"
@@ -179,7 +180,8 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const EriLau
 #endif
 
 // The digest reads P_bd, P_bc, P_ad, P_ac.  max of their max|P| (or 1 without the table):
-// 0 means the quartet contributes exactly nothing; the mixed-precision test uses it too.
+// 0 means the quartet contributes exactly nothing; the mixed-precision and the
+// density-weighted screening tests use it too.
 __device__ __forceinline__ double pmax4(const EriLaunch& L, int sa, int sb, int sc, int sd) {
   if (!L.pmax) return 1.0;
   const double* pm = L.pmax;
