@@ -1,5 +1,7 @@
-// Table-driven FP64 engine for contracted shell quartets (ab|cd) with the
-// erfc(omega r)/r kernel, fused with the exchange-matrix digest.
+// Table-driven engine for contracted shell quartets (ab|cd) with the erfc(omega r)/r
+// kernel, fused with the exchange-matrix digest.  It runs in FP64; the recurrence and
+// contraction steps are templated on the arithmetic type, so the mixed-precision kernel
+// runs them in FP32 for the quartets that qualify (the Boys step stays FP64).
 //
 // One "group" of G lanes (G = 1 or G = 32) evaluates one contracted quartet:
 //   1. for every surviving primitive quartet: the Boys step (G_m = F_m(T) -
