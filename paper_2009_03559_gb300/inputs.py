@@ -262,3 +262,91 @@ def make_system(kind: str, n_atoms: int, seed: int) -> System:
 
 def truncation_for(kind: str):
     return None if kind == "cluster" else 10.0
+
+
+# ---------------------------------------------------------------------------
+# Periodic images (the lattice sums of Eq. vx): a home cell, its lattice, and a real-space
+# density P^R between functions of the home cell and of the cell shifted by R.
+# ---------------------------------------------------------------------------
+
+@dataclass
+class PeriodicSystem:
+    """Home cell (``cell``: a System whose atoms lie in the home cell) and the lattice
+    (rows of ``lattice`` are the three cell vectors, bohr)."""
+
+    cell: System
+    lattice: np.ndarray
+
+    def shift(self, n) -> np.ndarray:
+        return np.asarray(n, dtype=np.float64) @ self.lattice
+
+
+def periodic_diamond(cells=(1, 1, 1), seed: int = 5000, a: float = 10.26, jitter: float = 0.05,
+                     spacing: float | None = None, tau: float = 1e-8, rcut: float = 6.0) -> PeriodicSystem:
+    """Diamond crystal: the home cell holds cells[0] x cells[1] x cells[2] conventional
+    8-atom cells (DZP-like shells as ``diamond_system``); lattice vectors are the home
+    cell's edges.  ``spacing`` (bohr) replaces the edge length of the lattice (not the atom
+    positions): a large spacing isolates the images."""
+    n = 8 * int(np.prod(cells))
+    rng = np.random.default_rng(seed)
+    sites = []
+    for i in range(cells[0]):
+        for j in range(cells[1]):
+            for k in range(cells[2]):
+                for b in range(8):
+                    sites.append(np.array([i, j, k], dtype=np.float64) + _DIAMOND_BASIS[b])
+    xyz = a * np.array(sites) + rng.uniform(-jitter, jitter, (n, 3))
+    sa, sl, sn, al, co = _draw_shells(rng, n, (0, 0, 1, 1, 2), 3, 0.08, 8.0)
+    cell = System(f"pdiamond{n}", xyz, sa, sl, sn, al, co, tau=tau, rcut=rcut, seed=seed, kind="diamond",
+                  rng_state=rng.bit_generator.state)
+    edge = np.array(cells, dtype=np.float64) * (a if spacing is None else spacing)
+    return PeriodicSystem(cell, np.diag(edge))
+
+
+def image_system(ps: PeriodicSystem, cell_list) -> System:
+    """The home cell's shells repeated in every cell of ``cell_list`` (cell-major order:
+    all shells of cell_list[0], then of cell_list[1], ...), the same exponents and weights."""
+    c = ps.cell
+    n_at = c.n_atoms
+    xyz = np.concatenate([c.xyz + ps.shift(n) for n in cell_list])
+    k = len(cell_list)
+    shell_atom = np.concatenate([c.shell_atom + i * n_at for i in range(k)]).astype(np.int32)
+    return System(f"{c.name}x{k}", xyz, shell_atom, np.tile(c.shell_l, k), np.tile(c.shell_nprim, k),
+                  np.tile(c.alpha, k), np.tile(c.coef, k), omega=c.omega, tau=c.tau, rcut=c.rcut,
+                  seed=c.seed, kind=c.kind)
+
+
+def periodic_density(ps: PeriodicSystem, r_cells: int, seed: int, truncate_bohr: float = 10.0,
+                     decay_bohr: float = 3.0) -> dict:
+    """Synthetic real-space density blocks P^R (n_bf x n_bf) for the cells R with every
+    |R_i| <= r_cells: N(0,1) values damped by exp(-d/decay_bohr), d the distance between
+    the two functions' atoms, zero beyond truncate_bohr, symmetrised so that
+    P^{-R} = (P^R)^T.  A stand-in for the Brillouin-zone integral of the paper's P^N."""
+    rng = np.random.default_rng(seed)
+    c = ps.cell
+    ba = c.bf_atom
+    cells = [(i, j, k) for i in range(-r_cells, r_cells + 1) for j in range(-r_cells, r_cells + 1)
+             for k in range(-r_cells, r_cells + 1)]
+    raw = {}
+    for R in cells:
+        d = np.linalg.norm(c.xyz[ba][:, None, :] - (c.xyz[ba] + ps.shift(R))[None, :, :], axis=-1)
+        m = rng.standard_normal((c.n_bf, c.n_bf)) * np.exp(-d / decay_bohr)
+        m[d > truncate_bohr] = 0.0
+        raw[R] = m
+    P = {}
+    for R in cells:
+        mR = tuple(-x for x in R)
+        P[R] = 0.5 * (raw[R] + raw[mR].T)
+    return P
+
+
+def periodic_sc(a: float = 6.0, seed: int = 5100, jitter: float = 0.3, tau: float = 1e-10,
+                rcut: float = 3.5, spacing: float | None = None) -> PeriodicSystem:
+    """Simple cubic crystal with one atom per cell (s and p shells, as ``cluster_system``):
+    the smallest periodic case.  ``spacing`` replaces the lattice constant of the images."""
+    rng = np.random.default_rng(seed)
+    xyz = rng.uniform(-jitter, jitter, (1, 3))
+    sa, sl, sn, al, co = _draw_shells(rng, 1, (0, 1), 3, 0.1, 20.0)
+    cell = System("psc1", xyz, sa, sl, sn, al, co, tau=tau, rcut=rcut, seed=seed, kind="cluster",
+                  rng_state=rng.bit_generator.state)
+    return PeriodicSystem(cell, np.eye(3) * (a if spacing is None else spacing))
