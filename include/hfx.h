@@ -117,7 +117,21 @@ typedef struct {
   double ms_build;             /* GPU time of the last hfx_build_K (zero K .. E_K ready) */
   double ms_class[21];         /* GPU time of each class launch in the last K build */
   double energy;               /* E_K = sum_{mu nu} P_{mu nu} K_{mu nu} of the last K build */
+  double flops_recurrence;     /* of flops_fp64 + flops_fp32: the recurrences alone (vertical
+                                  recurrence, contraction, horizontal recurrence, Cartesian ->
+                                  spherical step, digest into K), the primitive set-up excluded */
+  double special_evals;        /* Boys-function evaluations of the last timed build (each: F_m at
+                                  the top order and exp(-x) from the tables): two per evaluated
+                                  primitive quartet with the erfc kernel, one with omega = 0 */
+  int32_t streams_class[21];   /* warp kernel: primitive quartets run at a time per class */
+  int32_t reserved_stats[1];
 } hfx_stats;
+
+/* Primitive quartets the warp kernel runs at a time for quartet class cls (0..20) in later
+ * builds: 0 = the class default, else one of the variants the library carries (1, 2 or 4;
+ * the largest classes carry fewer).  Results do not depend on it (summation order aside).
+ * Errors: HFX_ERR_ARG for an unknown class or a variant the class does not carry. */
+int hfx_set_streams(hfx_ctx* ctx, int cls, int streams);
 
 /* Fills *opt with defaults: omega 0.11, tau 1e-10, no cutoff, prim_tau 1e-22, FP64,
  * dynamic schedule, zero-density-block skip on. */

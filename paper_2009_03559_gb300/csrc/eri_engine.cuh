@@ -39,20 +39,8 @@ __device__ __forceinline__ float sph_coef<float>(int i) { return kSphCoefF[i]; }
 template <>
 __device__ __forceinline__ double sph_coef<double>(int i) { return kSphCoef[i]; }
 
-// coefficient set of one primitive quartet (shared-memory layout for G > 1)
-enum {
-  CF_PA = 0, CF_WP = 3, CF_QC = 6, CF_WQ = 9,
-  CF_CA = 12,   // [n] = n/(2p), n = 0..3
-  CF_RP = 16,   // rho/p
-  CF_CK = 17,   // [n] = n/(2q), n = 0..3
-  CF_RQ = 21,   // rho/q
-  CF_CB = 22,   // [n] = n/(2(p+q)), n = 0..4
-  CF_G = 27,    // prefactor * G_m, m = 0..Lt
-  CF_SKIP = 36, // nonzero: primitive quartet negligible (kappa T beyond the table)
-  NCOEF = 37
-};
-
-// Coefficients held in registers (G = 1); selects avoid indexed register arrays.
+// Coefficients held in registers (one quartet per thread); selects avoid indexed
+// register arrays.
 struct CoefRg {
   double PA[3], WP[3], QC[3], WQ[3];
   double ca1, ca2, ca3, RP, ck1, ck2, ck3, RQ, cb1, cb2, cb3, cb4;
@@ -69,145 +57,142 @@ struct CoefRg {
   __device__ __forceinline__ double rq() const { return RQ; }
 };
 
-// Coefficients read from shared memory (G > 1), stored in the precision R of the
-// recurrences (FP64, or FP32 for quartets selected for FP32).
-template <typename R>
-struct CoefSm {
-  const R* c;
-  __device__ __forceinline__ R pa(int i) const { return c[CF_PA + i]; }
-  __device__ __forceinline__ R wp(int i) const { return c[CF_WP + i]; }
-  __device__ __forceinline__ R qc(int i) const { return c[CF_QC + i]; }
-  __device__ __forceinline__ R wq(int i) const { return c[CF_WQ + i]; }
-  __device__ __forceinline__ R ca(int n) const { return c[CF_CA + n]; }
-  __device__ __forceinline__ R ck(int n) const { return c[CF_CK + n]; }
-  __device__ __forceinline__ R cb(int n) const { return c[CF_CB + n]; }
-  __device__ __forceinline__ R rp() const { return c[CF_RP]; }
-  __device__ __forceinline__ R rq() const { return c[CF_RQ]; }
+// Scalars of one primitive quartet besides its Boys values.
+struct PrimScalars {
+  double RP, RQ, inv_s, PQ[3];
 };
 
-// Primitive-quartet set-up.  Fills the register coefficient set and returns the
-// prefactor-scaled attenuated Boys values in Gm[0..Lt]; returns false if the
-// primitive quartet is negligible (kappa T >= table end: G_m <= exp(-kappa T)).
-__device__ __forceinline__ bool prim_setup(const PrimPair& b, const PrimPair& k, int E, int F, int Lt,
-                                           double omega2, const double* __restrict__ tab, CoefRg& c,
-                                           double* Gm) {
+// Primitive-quartet set-up: the prefactor-scaled attenuated Boys values
+//   G_m = C_ab C_cd / sqrt(p+q) * (F_m(T) - kappa^{m+1/2} F_m(kappa T)),  m = 0..Lt,
+// kappa = omega^2 / (omega^2 + rho), T = rho |PQ|^2 (omega = 0: the Coulomb F_m(T)).  Both
+// Boys functions are taken at the top order only; the lower orders come from one downward
+// recursion on G itself: with A_m = pref F_m(T) and B_m = pref kappa^{m+1/2} F_m(kappa T),
+// F_{m-1}(x) = (2x F_m(x) + e^{-x}) / (2m-1) gives
+//   G_{m-1} = (2T G_m + pref e^{-T} - pref kappa^{m-1/2} e^{-kappa T}) / (2m-1).
+// Returns false if the quartet is negligible (kappa T beyond the tables: G_m < e^{-60}).
+__device__ __forceinline__ bool prim_core(const PrimPair& b, const PrimPair& k, int Lt, double omega, double omega2,
+                                          const double* __restrict__ tabs, double* G, PrimScalars& ps) {
   const double p = b.p, q = k.p;
   const double s = p + q;
-  const double inv_s = rcp_nr(s);
-  const double RP = q * inv_s;   // rho / p
-  const double RQ = p * inv_s;   // rho / q
-  const double rho = p * RP;
-  const double PQ0 = b.P[0] - k.P[0], PQ1 = b.P[1] - k.P[1], PQ2 = b.P[2] - k.P[2];
-  const double r2 = fma(PQ0, PQ0, fma(PQ1, PQ1, PQ2 * PQ2));
-  const double T = rho * r2;
-  double F1[kMaxLt + 1], F2[kMaxLt + 1];
-  const double pref = b.C * k.C * rsqrt_nr(s);
+  const double y = rsqrt_nr(s);   // 1/sqrt(p+q)
+  const double inv_s = y * y;
+  ps.inv_s = inv_s;
+  ps.RP = q * inv_s;              // rho / p
+  ps.RQ = p * inv_s;              // rho / q
+  const double rho = p * ps.RP;
+  ps.PQ[0] = b.P[0] - k.P[0];
+  ps.PQ[1] = b.P[1] - k.P[1];
+  ps.PQ[2] = b.P[2] - k.P[2];
+  const double T = rho * fma(ps.PQ[0], ps.PQ[0], fma(ps.PQ[1], ps.PQ[1], ps.PQ[2] * ps.PQ[2]));
+  const double pref = (b.C * k.C) * y;
+  const double* tabL = tabs + Lt * kBoysTableLen;
+  double F1, e1 = 0.0;
+  if (!ge_hi(T, kBoysXmaxHi))
+    boys_top(T, tabL, F1, e1);
+  else
+    F1 = boys_asym(Lt, T);
+  const double T2 = T + T;
   if (omega2 > 0.0) {
-    const double kap = omega2 * rcp_nr(omega2 + rho);
+    const double sk = omega * rsqrt_nr(omega2 + rho);   // sqrt(kappa)
+    const double kap = sk * sk;
     const double kT = kap * T;
-    if (kT >= kBoysXmax) return false;
-    boys_eval(Lt, T, tab, F1);
-    boys_eval(Lt, kT, tab, F2);
-    double a = pref * (kap * rsqrt_nr(kap));  // pref * kappa^{1/2}
+    if (ge_hi(kT, kBoysXmaxHi)) return false;
+    double F2, e2;
+    boys_top(kT, tabL, F2, e2);
+    // c[m] = pref kappa^{m-1/2}, m = 1..Lt+1
+    double c[kMaxLt + 2];
+    c[1] = pref * sk;
 #pragma unroll
-    for (int m = 0; m <= kMaxLt; ++m) {
+    for (int m = 1; m <= kMaxLt; ++m)
+      if (m <= Lt) c[m + 1] = c[m] * kap;
+    const double pe1 = pref * e1;
+    double g = 0.0;
+#pragma unroll
+    for (int m = 0; m <= kMaxLt; ++m)
+      if (m == Lt) g = fma(-c[m + 1], F2, pref * F1);
+    G[Lt] = g;
+#pragma unroll
+    for (int m = kMaxLt; m >= 1; --m) {
       if (m <= Lt) {
-        Gm[m] = fma(-a, F2[m], pref * F1[m]);
-        a *= kap;
+        g = fma(T2, g, fma(-c[m], e2, pe1)) * (1.0 / (2 * m - 1));
+        G[m - 1] = g;
       }
     }
   } else {
-    boys_eval(Lt, T, tab, F1);
+    const double pe1 = pref * e1;
+    double g = pref * F1;
+    G[Lt] = g;
 #pragma unroll
-    for (int m = 0; m <= kMaxLt; ++m)
-      if (m <= Lt) Gm[m] = pref * F1[m];
-  }
-  if (E > 0) {
-    c.PA[0] = b.PA[0]; c.PA[1] = b.PA[1]; c.PA[2] = b.PA[2];
-    c.WP[0] = -RP * PQ0; c.WP[1] = -RP * PQ1; c.WP[2] = -RP * PQ2;   // W - P
-    c.ca1 = b.inv2p; c.ca2 = b.inv2p + b.inv2p; c.ca3 = 3.0 * b.inv2p;
-    c.RP = RP;
-  }
-  if (F > 0) {
-    c.QC[0] = k.PA[0]; c.QC[1] = k.PA[1]; c.QC[2] = k.PA[2];
-    c.WQ[0] = RQ * PQ0; c.WQ[1] = RQ * PQ1; c.WQ[2] = RQ * PQ2;      // W - Q
-    c.ck1 = k.inv2p; c.ck2 = k.inv2p + k.inv2p; c.ck3 = 3.0 * k.inv2p;
-    c.RQ = RQ;
-    const double h = 0.5 * inv_s;
-    c.cb1 = h; c.cb2 = h + h; c.cb3 = 3.0 * h; c.cb4 = 4.0 * h;
+    for (int m = kMaxLt; m >= 1; --m) {
+      if (m <= Lt) {
+        g = fma(T2, g, pe1) * (1.0 / (2 * m - 1));
+        G[m - 1] = g;
+      }
+    }
   }
   return true;
 }
 
-// Set-up for the FP32 recurrences: the Boys step (rho, kappa, T, G_m, the prefactor) in FP64
-// exactly as in prim_setup, the VRR coefficients in FP32 from the float copies of the pair
-// data; only the G_m values are converted.  Writes the coefficient set cf (floats).
-__device__ __forceinline__ void prim_setup_f32(const PrimPair& b, const PrimPair& k, int E, int F, int Lt,
-                                               double omega2, const double* __restrict__ tab, float* cf) {
-  const double p = b.p, q = k.p;
-  const double s = p + q;
-  const double inv_s = rcp_nr(s);
-  const double rho = p * (q * inv_s);
-  const double PQ0 = b.P[0] - k.P[0], PQ1 = b.P[1] - k.P[1], PQ2 = b.P[2] - k.P[2];
-  const double T = rho * fma(PQ0, PQ0, fma(PQ1, PQ1, PQ2 * PQ2));
-  double F1[kMaxLt + 1], F2[kMaxLt + 1];
-  const double pref = b.C * k.C * rsqrt_nr(s);
-  if (omega2 > 0.0) {
-    const double kap = omega2 * rcp_nr(omega2 + rho);
-    const double kT = kap * T;
-    if (kT >= kBoysXmax) {
-      cf[CF_SKIP] = 1.f;
-      return;
-    }
-    boys_eval(Lt, T, tab, F1);
-    boys_eval(Lt, kT, tab, F2);
-    double a = pref * (kap * rsqrt_nr(kap));
-    for (int m = 0; m <= Lt; ++m) {
-      cf[CF_G + m] = (float)fma(-a, F2[m], pref * F1[m]);
-      a *= kap;
-    }
-  } else {
-    boys_eval(Lt, T, tab, F1);
-    for (int m = 0; m <= Lt; ++m) cf[CF_G + m] = (float)(pref * F1[m]);
-  }
-  cf[CF_SKIP] = 0.f;
-  const float pf = b.pf, qf = k.pf;
-  const float inv_sf = __frcp_rn(pf + qf);
-  const float RP = qf * inv_sf, RQ = pf * inv_sf;
-  const float d0 = (float)PQ0, d1 = (float)PQ1, d2 = (float)PQ2;
+// Set-up into registers (one quartet per thread).
+__device__ __forceinline__ bool prim_setup(const PrimPair& b, const PrimPair& k, int E, int F, int Lt, double omega,
+                                           double omega2, const double* __restrict__ tabs, CoefRg& c, double* Gm) {
+  PrimScalars ps;
+  if (!prim_core(b, k, Lt, omega, omega2, tabs, Gm, ps)) return false;
   if (E > 0) {
-    cf[CF_PA + 0] = b.PAf[0]; cf[CF_PA + 1] = b.PAf[1]; cf[CF_PA + 2] = b.PAf[2];
-    cf[CF_WP + 0] = -RP * d0; cf[CF_WP + 1] = -RP * d1; cf[CF_WP + 2] = -RP * d2;
-    cf[CF_CA + 1] = b.inv2pf; cf[CF_CA + 2] = 2.f * b.inv2pf; cf[CF_CA + 3] = 3.f * b.inv2pf;
-    cf[CF_RP] = RP;
+    c.PA[0] = b.PA[0]; c.PA[1] = b.PA[1]; c.PA[2] = b.PA[2];
+    c.WP[0] = -ps.RP * ps.PQ[0]; c.WP[1] = -ps.RP * ps.PQ[1]; c.WP[2] = -ps.RP * ps.PQ[2];   // W - P
+    c.ca1 = b.inv2p; c.ca2 = scale2(b.inv2p, 1); c.ca3 = b.inv2p3;
+    c.RP = ps.RP;
   }
   if (F > 0) {
-    cf[CF_QC + 0] = k.PAf[0]; cf[CF_QC + 1] = k.PAf[1]; cf[CF_QC + 2] = k.PAf[2];
-    cf[CF_WQ + 0] = RQ * d0; cf[CF_WQ + 1] = RQ * d1; cf[CF_WQ + 2] = RQ * d2;
-    cf[CF_CK + 1] = k.inv2pf; cf[CF_CK + 2] = 2.f * k.inv2pf; cf[CF_CK + 3] = 3.f * k.inv2pf;
-    cf[CF_RQ] = RQ;
-    const float h = 0.5f * inv_sf;
-    cf[CF_CB + 1] = h; cf[CF_CB + 2] = 2.f * h; cf[CF_CB + 3] = 3.f * h; cf[CF_CB + 4] = 4.f * h;
+    c.QC[0] = k.PA[0]; c.QC[1] = k.PA[1]; c.QC[2] = k.PA[2];
+    c.WQ[0] = ps.RQ * ps.PQ[0]; c.WQ[1] = ps.RQ * ps.PQ[1]; c.WQ[2] = ps.RQ * ps.PQ[2];      // W - Q
+    c.ck1 = k.inv2p; c.ck2 = scale2(k.inv2p, 1); c.ck3 = k.inv2p3;
+    c.RQ = ps.RQ;
+    c.cb1 = scale2(ps.inv_s, -1); c.cb2 = ps.inv_s; c.cb3 = 1.5 * ps.inv_s; c.cb4 = scale2(ps.inv_s, 1);
   }
+  return true;
 }
 
+// A coefficient set in group scratch (warp kernel) from the set-up values, in the precision
+// R of the recurrences: every set-up step runs in FP64; an FP32 set is the rounded FP64 one.
 template <typename R>
-__device__ __forceinline__ void store_coef(const CoefRg& c, const double* Gm, int Lt, bool ok, R* cf) {
-  cf[CF_SKIP] = ok ? R(0) : R(1);
-  if (!ok) return;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    cf[CF_PA + i] = c.PA[i];
-    cf[CF_WP + i] = c.WP[i];
-    cf[CF_QC + i] = c.QC[i];
-    cf[CF_WQ + i] = c.WQ[i];
-  }
-  cf[CF_CA + 1] = c.ca1; cf[CF_CA + 2] = c.ca2; cf[CF_CA + 3] = c.ca3; cf[CF_RP] = c.RP;
-  cf[CF_CK + 1] = c.ck1; cf[CF_CK + 2] = c.ck2; cf[CF_CK + 3] = c.ck3; cf[CF_RQ] = c.RQ;
-  cf[CF_CB + 1] = c.cb1; cf[CF_CB + 2] = c.cb2; cf[CF_CB + 3] = c.cb3; cf[CF_CB + 4] = c.cb4;
+__device__ __forceinline__ void write_set(const PrimPair& b, const PrimPair& k, int E, int F, int Lt,
+                                          const double* G, const PrimScalars& ps, R* cf) {
 #pragma unroll
   for (int m = 0; m <= kMaxLt; ++m)
-    if (m <= Lt) cf[CF_G + m] = Gm[m];
+    if (m <= Lt) cf[HFX_CF_G + m] = R(G[m]);
+  cf[HFX_CF_ONE] = R(1);
+  cf[HFX_CF_ZERO] = R(0);
+  cf[HFX_CF_CA] = R(0);
+  cf[HFX_CF_CK] = R(0);
+  cf[HFX_CF_CB] = R(0);
+  if (E > 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      cf[HFX_CF_PA + i] = R(b.PA[i]);
+      cf[HFX_CF_WP + i] = R(-ps.RP * ps.PQ[i]);
+    }
+    cf[HFX_CF_CA + 1] = R(b.inv2p);
+    cf[HFX_CF_CA + 2] = R(scale2(b.inv2p, 1));
+    cf[HFX_CF_CA + 3] = R(b.inv2p3);
+    cf[HFX_CF_RP] = R(ps.RP);
+  }
+  if (F > 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      cf[HFX_CF_QC + i] = R(k.PA[i]);
+      cf[HFX_CF_WQ + i] = R(ps.RQ * ps.PQ[i]);
+    }
+    cf[HFX_CF_CK + 1] = R(k.inv2p);
+    cf[HFX_CF_CK + 2] = R(scale2(k.inv2p, 1));
+    cf[HFX_CF_CK + 3] = R(k.inv2p3);
+    cf[HFX_CF_RQ] = R(ps.RQ);
+    cf[HFX_CF_CB + 1] = R(scale2(ps.inv_s, -1));
+    cf[HFX_CF_CB + 2] = R(ps.inv_s);
+    cf[HFX_CF_CB + 3] = R(1.5 * ps.inv_s);
+    cf[HFX_CF_CB + 4] = R(scale2(ps.inv_s, 1));
+  }
 }
 
 __device__ __forceinline__ uint4 ld_op(const uint32_t* base, int idx) {
@@ -248,6 +233,35 @@ __device__ __forceinline__ void vrr_ket(uint4 op, R* V, R* S, int st, const Coef
     S[dst * st] = v;
   else
     V[dst * st] = v;
+}
+
+// One entry of a warp schedule (gen_eri_tables.py): this lane's op in the current iteration,
+// on the region X of its stream, with the coefficient set of the primitive quartet that
+// stream runs (sets j + u of the chunk; set 32, all zeros, once the chunk is used up).
+// The shape bits (11, 12) are the same on every valid lane of an iteration, so the optional
+// terms are warp-uniform branches; ops of a simpler shape in such an iteration read the
+// zero coefficient n = 0 and the zero slot.
+template <typename R>
+__device__ __forceinline__ void sched_op(uint4 e, R* S, int rsz, int zero, const R* CF, int j, int nv) {
+  const uint32_t w = e.w;
+  if (!(w & (1u << 10))) return;
+  const int u = (w >> 13) & 7;
+  const int p = j + u;
+  const R* cf = CF + (p < nv ? p : 32) * HFX_NCOEF;
+  R* X = S + u * rsz;
+  const int base = (w & (1u << 7)) ? HFX_CF_KET_BASE : 0;
+  const int dir = w & 3;
+  const bool add = (w >> 9) & 1;
+  const int i1 = add ? HFX_CF_ONE : base + HFX_CF_PA + dir;
+  const int i2 = add ? HFX_CF_ZERO : base + HFX_CF_WP + dir;
+  const int dst = e.x & 0xFFFF;
+  const int s0 = ((w >> 8) & 1) ? dst : zero;
+  R v = fmar(cf[i1], X[e.x >> 16], X[s0]);
+  v = fmar(cf[i2], X[e.y & 0xFFFF], v);
+  if (w & (1u << 11))
+    v = fmar(cf[base + HFX_CF_CA + ((w >> 2) & 3)], fmar(-cf[base + HFX_CF_RP], X[e.z & 0xFFFF], X[e.y >> 16]), v);
+  if (w & (1u << 12)) v = fmar(cf[HFX_CF_CB + ((w >> 4) & 7)], X[e.z >> 16], v);
+  X[dst] = v;
 }
 
 // Post-contraction op on the group scratch S.

@@ -391,7 +391,7 @@ class ClassTables:
         for lvl in self.ket_ops:
             for o in lvl:
                 vrr += 3 + (4 if o["nA"] else 0) + (2 if o["nB"] else 0)
-        acc = self.n_acc - self.n_folded
+        acc = self.n_acc          # one add per accumulator (inside an FMA when folded)
         hrr = sph = 0
         for st in self.stages:
             for _, srcs, _ in st["ops"]:
@@ -411,14 +411,247 @@ class ClassTables:
         """Group scratch (doubles): acc block at 0 and the VRR slots after it while the
         primitive loop runs; afterwards the stages alternate between the bottom (offset
         0) and the top (ending at the scratch size) of the same scratch."""
+        T, bases = self.post_layout()
+        return max(T, self.n_acc + self.n_vrr_slots), bases
+
+    def post_layout(self):
+        """Scratch of the post-contraction stages alone: the largest two consecutive stage
+        blocks (the first being the accumulators at offset 0), and the stage offsets."""
         sizes = self.stage_sizes
-        T = self.n_acc + self.n_vrr_slots
+        T = sizes[0]
         for k in range(1, len(sizes)):
             T = max(T, sizes[k - 1] + sizes[k])
         bases = [0]
         for k in range(1, len(sizes)):
             bases.append(T - sizes[k] if k % 2 == 1 else 0)
         return T, bases
+
+
+# ---------------------------------------------------------------------------------------
+# Warp schedules.  A warp runs k primitive quartets ("streams") of one contracted quartet at
+# a time; each stream owns a region of group scratch: [accumulators | VRR slots | a zero
+# slot].  The VRR ops of all streams, and one add per accumulator whose target another op
+# reads, are list-scheduled into iterations of at most 32 ops (one per lane).  The FP64
+# pipe of this part charges every warp instruction in full whatever the number of active
+# lanes, and an iteration costs the union of its lanes' instruction sequences, so the
+# scheduler packs each iteration with ops of one shape:
+#   2 instructions (leading FMA from the accumulator or the zero slot, then the W term),
+#   +2 with the n/(2p) (V3 - rho/p V4) term, +1 with the e_i/(2(p+q)) V5 term.
+# Targets that no op reads accumulate in their producing op (its first FMA starts from the
+# accumulator), so the contraction costs no separate add for them.
+# Coefficient-set layout (per primitive quartet, doubles or floats):
+CF = dict(PA=0, WP=3, CA=6, RP=10, QC=11, WQ=14, CK=17, RQ=21, CB=22, ONE=27, ZERO=28, G=29)
+NCOEF = 39            # 38 used; odd so that the lanes' sets start in different banks
+KET_BASE = CF["QC"] - CF["PA"]
+SCHED_KS = (1, 2, 4)
+SCHED_MAX_REGION_DOUBLES = 3600   # k * region limit for a variant to be generated
+
+
+def shape_cost(a, b):
+    return 2 + 2 * a + b
+
+
+class WarpSchedule:
+    def __init__(self, c, k):
+        self.c, self.k = c, k
+        n_acc, nvs = c.n_acc, c.n_vrr_slots
+        self.zero = n_acc + nvs   # before slot assignment: a slot past the VRR slots
+        nb = len(c.bra_ops)
+        ops = []             # (dst_region, fold, s1..s5 region, dir, nA, nB, ket, add, deps(op ids), level)
+        writer = {}
+        lv_all = c.bra_ops + c.ket_ops
+        for li, lv in enumerate(lv_all):
+            for o in lv:
+                writer[o["dst"]] = len(writer)
+        # read set of VRR slots
+        read = set()
+        for li, lv in enumerate(lv_all):
+            ket = li >= nb
+            for o in lv:
+                read.update(o["s"][:2])
+                if o["nA"]:
+                    read.update(o["s"][2:4])
+                if ket and o["nB"]:
+                    read.add(o["s"][4])
+        acc_of = {}
+        for a, (e, f) in enumerate((e, f) for e in c.e_list for f in c.f_list):
+            acc_of[c.slot[(e, f, 0)]] = a
+        opid = {}
+        for li, lv in enumerate(lv_all):
+            ket = li >= nb
+            for o in lv:
+                d = o["dst"]
+                fold = d in acc_of and d not in read
+                srcs = [o["s"][0], o["s"][1]]
+                srcs += [o["s"][2], o["s"][3]] if o["nA"] else [None, None]
+                srcs += [o["s"][4]] if (ket and o["nB"]) else [None]
+                deps = set(opid[s] for s in srcs if s is not None and s in opid)
+                reg = [n_acc + s if s is not None else self.zero for s in srcs]
+                opid[d] = len(ops)
+                ops.append(dict(dst=acc_of[d] if fold else n_acc + d, fold=fold, s=reg, dir=o["dir"],
+                                nA=o["nA"], nB=o["nB"] if ket else 0, ket=int(ket), add=0, deps=deps,
+                                A=int(o["nA"] > 0), B=int(ket and o["nB"] > 0)))
+        # adds for accumulators whose target is read (or is a base slot)
+        for sl, a in sorted(acc_of.items(), key=lambda t: t[1]):
+            if sl in opid and ops[opid[sl]]["fold"]:
+                continue
+            deps = {opid[sl]} if sl in opid else set()
+            ops.append(dict(dst=a, fold=True, s=[n_acc + sl, self.zero, self.zero, self.zero, self.zero],
+                            dir=0, nA=0, nB=0, ket=0, add=1, deps=deps, A=0, B=0))
+        self.ops = ops
+        # longest path to a sink (critical-path priority)
+        h = [0] * len(ops)
+        succ = [[] for _ in ops]
+        for i, o in enumerate(ops):
+            for d in o["deps"]:
+                succ[d].append(i)
+        for i in reversed(range(len(ops))):
+            h[i] = 1 + max((h[j] for j in succ[i]), default=0)
+        self.height = h
+        self.schedule()
+
+    def schedule(self):
+        ops, k = self.ops, self.k
+        n = len(ops)
+        ndep = [[len(o["deps"]) for o in ops] for _ in range(k)]
+        succ = [[] for _ in ops]
+        for i, o in enumerate(ops):
+            for d in o["deps"]:
+                succ[d].append(i)
+        ready = [(u, i) for u in range(k) for i in range(n) if ndep[u][i] == 0]
+        iters = []
+        cost = 0
+        left = k * n
+        while left:
+            best = None
+            for cap in ((0, 0), (1, 0), (0, 1), (1, 1)):
+                cand = [t for t in ready if ops[t[1]]["A"] <= cap[0] and ops[t[1]]["B"] <= cap[1]]
+                if not cand:
+                    continue
+                cand.sort(key=lambda t: (-self.height[t[1]], t[0], t[1]))
+                cand = cand[:32]
+                ea = max(ops[t[1]]["A"] for t in cand)
+                eb = max(ops[t[1]]["B"] for t in cand)
+                score = len(cand) / shape_cost(ea, eb)
+                if best is None or score > best[0] + 1e-12:
+                    best = (score, cand, ea, eb)
+            _, it, ea, eb = best
+            cost += shape_cost(ea, eb)
+            iters.append((it, ea, eb))
+            sel = set(it)
+            ready = [t for t in ready if t not in sel]
+            for (u, i) in it:
+                for j in succ[i]:
+                    ndep[u][j] -= 1
+                    if ndep[u][j] == 0:
+                        ready.append((u, j))
+            left -= len(it)
+        self.iters = iters
+        self.cost = cost
+        self.assign_slots()
+        # every stream's accumulators: each written by exactly one entry per stream
+        seen = set()
+        for it, _, _ in iters:
+            for (u, i) in it:
+                o = ops[i]
+                if o["fold"]:
+                    key = (u, o["dst"])
+                    assert key not in seen
+                    seen.add(key)
+        assert len(seen) == k * self.c.n_acc, (self.c.name(), k)
+
+    def assign_slots(self):
+        """Physical slots of each stream's region: accumulators [0, n_acc), the base values
+        G_m [n_acc, n_acc + Lt + 1), the zero slot, then the VRR values, each holding a slot
+        from the iteration that writes it to the last iteration that reads it (a slot freed
+        by the reads of iteration t is written again at t + 1 at the earliest)."""
+        c, k = self.c, self.k
+        n_acc, nbase = c.n_acc, c.Lt + 1
+        zero = n_acc + nbase
+        first = zero + 1
+        base_old = {n_acc + m: n_acc + m for m in range(nbase)}
+        old_zero = self.zero
+        # last reading iteration of each (stream, old slot)
+        last = {}
+        for t, (it, ea, eb) in enumerate(self.iters):
+            for (u, i) in it:
+                o = self.ops[i]
+                for sl in o["s"]:
+                    if sl >= n_acc and sl != old_zero and sl not in base_old:
+                        last[(u, sl)] = t
+        phys = {}           # (u, old slot) -> physical slot
+        free = [[] for _ in range(k)]
+        top = [first] * k
+        release = {}        # iteration -> [(u, phys)]
+        mapped = []         # per iteration: entries (u, i, dst, srcs)
+        for t, (it, ea, eb) in enumerate(self.iters):
+            for (u, p) in release.pop(t - 1, []):
+                free[u].append(p)
+            for u in range(k):
+                free[u].sort(reverse=True)
+            row = []
+            for (u, i) in it:
+                o = self.ops[i]
+                src = []
+                for sl in o["s"]:
+                    if sl == old_zero:
+                        src.append(zero)
+                    elif sl < n_acc or sl in base_old:
+                        src.append(sl)
+                    else:
+                        src.append(phys[(u, sl)])
+                row.append((u, i, src))
+            for (u, i, src) in row:
+                o = self.ops[i]
+                if o["fold"]:
+                    dst = o["dst"]
+                else:
+                    key = (u, o["dst"])
+                    if free[u]:
+                        dst = free[u].pop()
+                    else:
+                        dst = top[u]
+                        top[u] += 1
+                    phys[key] = dst
+                    lt = last.get(key, t)
+                    release.setdefault(lt, []).append((u, dst))
+                mapped.append((t, u, i, dst, src))
+        self.mapped = mapped
+        self.zero = zero
+        T, _ = c.post_layout()
+        rsz = max(top)
+        if rsz % 2 == 0:
+            rsz += 1
+        self.rsz = rsz
+        self.group = max(k * rsz, T)    # the post-contraction stages use the first T doubles
+
+    def words(self):
+        out = []
+        by_iter = {}
+        for (t, u, i, dst, src) in self.mapped:
+            by_iter.setdefault(t, []).append((u, i, dst, src))
+        for t, (it, ea, eb) in enumerate(self.iters):
+            ents = by_iter.get(t, [])
+            for lane in range(32):
+                if lane < len(ents):
+                    u, i, dst, s = ents[lane]
+                    o = self.ops[i]
+                    w = (o["dir"] | (o["nA"] << 2) | (o["nB"] << 4) | (o["ket"] << 7) | (int(o["fold"]) << 8)
+                         | (o["add"] << 9) | (1 << 10) | (ea << 11) | (eb << 12) | (u << 13))
+                    out += [dst | (s[0] << 16), s[1] | (s[2] << 16), s[3] | (s[4] << 16), w]
+                else:
+                    out += [0, 0, 0, (ea << 11) | (eb << 12)]
+        return out
+
+
+def warp_schedules(c):
+    """The generated variants (k = 1, 2, 4 streams) whose scratch stays within the limit."""
+    out = {}
+    for k in SCHED_KS:
+        ws = WarpSchedule(c, k)
+        if k == 1 or ws.group <= SCHED_MAX_REGION_DOUBLES:
+            out[k] = ws
+    return out
 
 
 def pack_vrr(o):
@@ -518,6 +751,38 @@ def emit(classes, f=sys.stdout):
             str(r["out_base"]), lst(c.final_dims, 4),
             str(fl["vrr"] + fl["acc"]), str(fl["hrr"] + fl["sph"] + fl["digest"]), str(fl["digest"]),
         ]) + "},\n")
+    w("};\n\n")
+    # warp schedules
+    w("// Coefficient set of one primitive quartet (group scratch of the warp kernel)\n")
+    for name, v in CF.items():
+        w(f"#define HFX_CF_{name} {v}\n")
+    w(f"#define HFX_NCOEF {NCOEF}\n")
+    w(f"#define HFX_CF_KET_BASE {KET_BASE}\n\n")
+    sched_words, info = [], []
+    for c in classes:
+        row = []
+        ws = warp_schedules(c)
+        for k in SCHED_KS:
+            if k in ws:
+                v = ws[k]
+                row.append((k, v.rsz, v.zero, len(v.iters), len(sched_words) // 4, v.group, v.cost))
+                sched_words.extend(v.words())
+            else:
+                row.append((0, 0, 0, 0, 0, 0, 0))
+        info.append((c, row))
+    w("// Warp schedules: per entry (uint4) dst | s1 << 16, s2 | s3 << 16, s4 | s5 << 16, flags\n")
+    w("// (dir | nA << 2 | nB << 4 | ket << 7 | fold << 8 | add << 9 | valid << 10 | shapeA << 11 |\n")
+    w("//  shapeB << 12 | stream << 13); 32 entries per iteration.\n")
+    sched_words.extend([0] * (32 * 4))   # padding iteration: the warp kernel prefetches one past the end
+    w(f"HFX_TABLE_QUAL uint32_t kSched[{len(sched_words)}] = {{\n")
+    for i in range(0, len(sched_words), 8):
+        w("  " + ", ".join(f"0x{x:x}u" for x in sched_words[i:i + 8]) + ",\n")
+    w("};\n\n")
+    w(f"static const SchedVariant kSchedInfo[HFX_N_CLASSES][{len(SCHED_KS)}] = {{\n")
+    for c, row in info:
+        costs = ", ".join(f"k{r[0]} {r[6] / max(r[0], 1):.1f}" for r in row if r[0])
+        w(f"  // ({c.name()}) FP64 warp instructions per primitive quartet: {costs}\n")
+        w("  {" + ", ".join("{" + ", ".join(str(x) for x in r[:6]) + "}" for r in row) + "},\n")
     w("};\n")
 
 

@@ -120,7 +120,7 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
   int r;
   if ((r = ctx->alloc(&ctx->d_xyz, 3 * (size_t)n_atoms)) || (r = ctx->alloc(&ctx->d_alpha, np)) ||
       (r = ctx->alloc(&ctx->d_coef, np)) || (r = ctx->alloc(&ctx->d_w, np)) ||
-      (r = ctx->alloc(&ctx->d_boys, (size_t)kBoysRows * kBoysCols)) || (r = ctx->alloc(&ctx->d_atom, n_shells)) ||
+      (r = ctx->alloc(&ctx->d_boys, (size_t)(kMaxLt + 1) * kBoysTableLen)) || (r = ctx->alloc(&ctx->d_atom, n_shells)) ||
       (r = ctx->alloc(&ctx->d_l, n_shells)) || (r = ctx->alloc(&ctx->d_nprim, n_shells)) ||
       (r = ctx->alloc(&ctx->d_prim_off, n_shells)) || (r = ctx->alloc(&ctx->d_bf_off, n_shells)) ||
       (r = ctx->alloc(&ctx->d_energy, 1)) || (r = ctx->alloc(&ctx->d_busy, 1024)) ||
@@ -157,21 +157,23 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
   return HFX_OK;
 }
 
-// FP64 flops (add/mul 1, fma 2) of one primitive-quartet set-up as written in
-// prim_setup / boys_eval (table branch; the asymptotic branch is not cheaper).
-static double boys_flops(int mmax) { return mmax <= 1 ? 7.0 + 12.0 * (mmax + 1) : 32.0 + 3.0 * mmax; }
+// Flops (add/mul 1, fma 2) of one primitive-quartet set-up as written in prim_core and
+// write_set, with the table branch of both Boys evaluations (each: the offset from the
+// grid point and two seven-term Horner chains, 25 flops; the asymptotic branch taken for
+// T >= 60 costs 7 + 2 Lt and is not counted separately).
 static double setup_flops(int E, int F, int Lt, bool erfc) {
-  double f = 1 + 4 + 3 + 9 + 6 + 2;                    // s, 1/s, rho/p, rho/q, rho, PQ, r2, T, rsqrt, pref
+  // s, rsqrt(s), 1/s, rho/p, rho/q, rho, PQ, r2, T, pref, Boys(T), 2T
+  double f = 1 + 5 + 1 + 2 + 1 + 3 + 5 + 1 + 2 + 25 + 1;
   if (erfc)
-    f += 7 + 7 + 2 * boys_flops(Lt) + 4.0 * (Lt + 1);    // kappa, kappa^{1/2}, two Boys, G_m
+    f += 7 + 1 + 1 + 25 + 1 + Lt + 1 + 3 + 5.0 * Lt;  // sqrt(kappa), kappa, kT, Boys(kT), c_m, G recursion
   else
-    f += boys_flops(Lt) + (Lt + 1);
-  if (E > 0) f += 5;
-  if (F > 0) f += 9;
+    f += 1 + 1 + 3.0 * Lt;
+  if (E > 0) f += 3;   // W - P
+  if (F > 0) f += 4;   // W - Q, 3/(2(p+q))
   return f;
 }
 // a primitive quartet dropped at kappa T >= table end costs the set-up up to that test
-static double skip_flops() { return 1 + 4 + 3 + 9 + 6 + 2 + 7; }
+static double skip_flops() { return 47 + 7 + 1 + 1; }
 
 EriLaunch hfx::base_launch(hfx_ctx* ctx) {
   EriLaunch L;
@@ -185,16 +187,17 @@ EriLaunch hfx::base_launch(hfx_ctx* ctx) {
   L.sh.bf_off = ctx->d_bf_off;
   L.sh.atom = ctx->d_atom;
   L.boys = ctx->d_boys;
+  L.omega = ctx->opt.omega;
   L.omega2 = ctx->opt.omega * ctx->opt.omega;
   L.schedule = ctx->opt.schedule;
   return L;
 }
 
 static int grid_for(hfx_ctx* ctx, int cls, int mode, long long work_items, int gs, bool mixed = false,
-                    bool batch = false) {
+                    bool batch = false, int streams = 0) {
   const int groups_per_block = eri_groups_per_block(mode, gs, mixed);
   long long need = (work_items + groups_per_block - 1) / groups_per_block;
-  long long cap = (long long)eri_blocks_per_sm(cls, mode, gs, mixed, batch) * ctx->n_sm;
+  long long cap = (long long)eri_blocks_per_sm(cls, mode, gs, mixed, batch, streams) * ctx->n_sm;
   long long g = std::min(need, cap);
   return (int)std::max(1LL, g);
 }
@@ -452,10 +455,13 @@ static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int pa
     int gs = ctx->gs_override[cp] ? ctx->gs_override[cp] : eri_group_size(cp);
     if (force32) gs = 32;
     ctx->gs_used[cp] = gs;
+    const int streams = ctx->streams_override[cp];
+    ctx->streams_used[cp] = gs == 32 ? eri_streams(cp, streams) : 0;
     L.chunk = gs == 1 ? 256 : 8;
     const long long items = ctx->opt.schedule == HFX_SCHED_PAIR ? (L.row_end - L.row_begin) : L.q_count;
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[2 + 2 * cp], s));
-    CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items, gs, force32), s, gs, force32, false));
+    CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items, gs, force32, false, streams), s, gs, force32, false,
+                  streams));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3 + 2 * cp], s));
     ctx->class_launched[cp] = true;
   }
@@ -494,6 +500,14 @@ extern "C" int hfx_set_group_size(hfx_ctx* ctx, int cls, int gs) {
   return HFX_OK;
 }
 
+extern "C" int hfx_set_streams(hfx_ctx* ctx, int cls, int streams) {
+  if (!ctx) return HFX_ERR_ARG;
+  if (cls < 0 || cls >= 21 || streams < 0 || !eri_streams_valid(cls, streams))
+    return ctx->fail(HFX_ERR_ARG, "class must be 0..20 and streams 0 or a variant the class carries");
+  ctx->streams_override[cls] = streams;
+  return HFX_OK;
+}
+
 extern "C" int hfx_set_timing(hfx_ctx* ctx, int enable) {
   if (!ctx) return HFX_ERR_ARG;
   ctx->timing = enable != 0;
@@ -504,15 +518,17 @@ extern "C" int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out) {
   if (!ctx || !out) return HFX_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->stream));
   hfx_stats& st = ctx->stats;
-  for (int cp = 0; cp < 21; ++cp)
+  for (int cp = 0; cp < 21; ++cp) {
     st.group_size_class[cp] = ctx->gs_used[cp] ? ctx->gs_used[cp] : eri_group_size(cp);
+    st.streams_class[cp] = ctx->streams_used[cp];
+  }
   CK(cudaMemcpy(&st.energy, ctx->d_energy, sizeof(double), cudaMemcpyDeviceToHost));
   if (ctx->timing) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) st.ms_build = ms;
     unsigned long long cnt[kNCnt * 21];
     CK(cudaMemcpy(cnt, ctx->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
-    double fl = 0.0, fl32 = 0.0;
+    double fl = 0.0, fl32 = 0.0, flr = 0.0, nsp = 0.0;
     for (int cp = 0; cp < 21; ++cp) {
       st.ms_class[cp] = 0.0;
       if (ctx->class_launched[cp] && cudaEventElapsedTime(&ms, ctx->ev[2 + 2 * cp], ctx->ev[3 + 2 * cp]) == cudaSuccess)
@@ -532,9 +548,13 @@ extern "C" int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out) {
       st.flops_class[cp] = f64 + f32;
       fl += f64;
       fl32 += f32;
+      flr += (double)c[0] * ci.flops_prim + (double)c[1] * ci.flops_quartet;
+      nsp += (double)c[0] * (ctx->opt.omega > 0.0 ? 2.0 : 1.0) + (double)c[2];
     }
     st.flops_fp64 = fl;
     st.flops_fp32 = fl32;
+    st.flops_recurrence = flr;
+    st.special_evals = nsp;
   }
   *out = st;
   return HFX_OK;

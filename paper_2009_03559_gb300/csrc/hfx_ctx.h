@@ -44,6 +44,8 @@ struct hfx_ctx {
   bool class_launched[21] = {};
   int gs_override[21] = {};  // lanes per quartet chosen by the caller per class (0 = default)
   int gs_used[21] = {};      // lanes per quartet of each class in the last build
+  int streams_override[21] = {};  // warp kernel: primitive quartets at a time (0 = default)
+  int streams_used[21] = {};
   hfx_stats stats{};
   float ms_pairs = 0.f;
   std::vector<void*> allocs;       // owned for the context lifetime

@@ -21,7 +21,7 @@ const EriClassInfo* class_info_host() { return kClassInfo; }
 __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaunch& L, int bra, int ket, double* S,
                                            int st) {
   const PairArrays pa = L.pa;
-  const double omega2 = L.omega2;
+  const double omega = L.omega, omega2 = L.omega2;
   const double* boys = L.boys;
   double* V = S + ci.work_base * st;
   const int nb = __ldg(pa.prim_n + bra), nk = __ldg(pa.prim_n + ket);
@@ -35,7 +35,7 @@ __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaun
       const PrimPair k = pk[ik];
       CoefRg c;
       double Gm[kMaxLt + 1];
-      if (!prim_setup(b, k, ci.E, ci.F, ci.Lt, omega2, boys, c, Gm)) continue;
+      if (!prim_setup(b, k, ci.E, ci.F, ci.Lt, omega, omega2, boys, c, Gm)) continue;
       ++any;
       for (int m = 0; m <= ci.Lt; ++m) V[m * st] = Gm[m];
       for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
@@ -66,15 +66,15 @@ __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaun
 }
 
 // ---------------------------------------------------------------------------
-// Contracted quartet, G = GS (8, 16 or 32 lanes of one warp, gm = their lane mask): the
-// group owns the quartet.  Lanes set up GS primitive quartets at a time (coefficient sets
-// in shared memory), then share the ops of each recurrence level.  Smaller groups keep
-// more lanes busy in classes whose recurrence levels have few ops.
+// Contracted quartet, one warp: lanes set up 32 primitive quartets at a time (coefficient
+// sets in group scratch, compacted so that negligible ones take no place), then the warp
+// runs the class's schedule over k of them at a time (k streams, each with its own region
+// of accumulators and VRR slots), and finally sums the streams' accumulators.
 // ---------------------------------------------------------------------------
 // HRR and Cartesian -> spherical stages on the group scratch S (lanes share each stage)
-template <typename R, int GS>
+template <typename R>
 __device__ __forceinline__ void post_stages(const EriClassInfo& ci, const PairArrays& pa, int bra, int ket, R* S,
-                                            int lane, unsigned gm) {
+                                            int lane) {
   R AB[3], CD[3];
   for (int i = 0; i < 3; ++i) {
     AB[i] = R(__ldg(pa.AB + 3 * bra + i));
@@ -82,79 +82,94 @@ __device__ __forceinline__ void post_stages(const EriClassInfo& ci, const PairAr
   }
   for (int s = 0; s < ci.n_post; ++s) {
     const int off = ci.post_off[s], n = ci.post_n[s], type = ci.post_type[s];
-    for (int o = lane; o < n; o += GS) post_op<R>(ld_op(kPostOps, off + o), type, S, 1, AB, CD);
-    __syncwarp(gm);
+    for (int o = lane; o < n; o += 32) post_op<R>(ld_op(kPostOps, off + o), type, S, 1, AB, CD);
+    __syncwarp();
   }
 }
 
-template <typename R, bool FOLD, int GS>
-__device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const EriLaunch& L, int bra, int ket, R* S, R* CF,
-                                            int lane, unsigned gm) {
+// Group scratch of one warp (in doubles): k stream regions, 33 coefficient sets (the last
+// one all zeros), one spare double.
+__host__ __device__ __forceinline__ int g32_stride(const SchedVariant& sv) {
+  return sv.group + 33 * HFX_NCOEF + 1;
+}
+
+template <typename R>
+__device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedVariant& sv, const EriLaunch& L,
+                                            int bra, int ket, R* S, R* CF, int lane) {
   const PairArrays pa = L.pa;
-  const double omega2 = L.omega2;
+  const double omega = L.omega, omega2 = L.omega2;
   const double* boys = L.boys;
-  R* V = S + ci.work_base;
   const int nb = __ldg(pa.prim_n + bra), nk = __ldg(pa.prim_n + ket);
   const PrimPair* pb = pa.prim + __ldg(pa.prim_off + bra);
   const PrimPair* pk = pa.prim + __ldg(pa.prim_off + ket);
-  for (int a = lane; a < ci.n_acc; a += GS) S[a] = R(0);
+  const int k = sv.k, rsz = sv.rsz, nacc = ci.n_acc, nbase = ci.Lt + 1;
+  for (int i = lane; i < k * nacc; i += 32) {
+    const int u = i / nacc;
+    S[u * rsz + (i - u * nacc)] = R(0);
+  }
+  if (lane < k) S[lane * rsz + sv.zero] = R(0);
+  // coefficient set 32: all zeros, for streams past the chunk's last primitive quartet (the
+  // FP32 and FP64 views of the group memory overlap, so it is laid down per quartet)
+  for (int i = lane; i < HFX_NCOEF; i += 32) CF[32 * HFX_NCOEF + i] = R(0);
+  const uint4* sched = reinterpret_cast<const uint4*>(kSched) + sv.off;
   const int npq = nb * nk;
   int any = 0;
-  for (int base = 0; base < npq; base += GS) {
+  for (int base = 0; base < npq; base += 32) {
     const int t = base + lane;
+    double G[kMaxLt + 1];
+    PrimScalars ps;
+    int ib = 0, ik = 0;
+    bool ok = false;
     if (t < npq) {
-      const int ib = t / nk, ik = t - ib * nk;
-      // the Boys step and the quantities feeding it stay in FP64 in either precision
-      if constexpr (sizeof(R) == 4) {
-        prim_setup_f32(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, omega2, boys, reinterpret_cast<float*>(CF + lane * NCOEF));
-      } else {
-        CoefRg c;
-        double Gm[kMaxLt + 1];
-        const bool ok = prim_setup(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, omega2, boys, c, Gm);
-        store_coef<R>(c, Gm, ci.Lt, ok, CF + lane * NCOEF);
+      ib = t / nk;
+      ik = t - ib * nk;
+      ok = prim_core(pb[ib], pk[ik], ci.Lt, omega, omega2, boys, G, ps);
+    }
+    const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    if (ok)
+      write_set<R>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps, CF + __popc(okm & ((1u << lane) - 1u)) * HFX_NCOEF);
+    const int nv = __popc(okm);
+    any += nv;
+    __syncwarp();
+    for (int j = 0; j < nv; j += k) {
+      for (int i = lane; i < k * nbase; i += 32) {
+        const int u = i / nbase, m = i - u * nbase;
+        S[u * rsz + nacc + m] = (j + u < nv) ? CF[(j + u) * HFX_NCOEF + HFX_CF_G + m] : R(0);
+      }
+      __syncwarp();
+      uint4 e = __ldg(sched + lane);
+      for (int it = 1; it <= sv.n_iter; ++it) {
+        // the next entry is fetched before this one runs (the last fetch reads one
+        // iteration past the variant's table: the tables end with a padding iteration)
+        const uint4 en = __ldg(sched + it * 32 + lane);
+        sched_op<R>(e, S, rsz, sv.zero, CF, j, nv);
+        __syncwarp();
+        e = en;
       }
     }
-    __syncwarp(gm);
-    const int nchunk = min(GS, npq - base);
-    for (int u = 0; u < nchunk; ++u) {
-      const R* cf = CF + u * NCOEF;
-      if (cf[CF_SKIP] != R(0)) continue;
-      ++any;
-      const CoefSm<R> c{cf};
-      for (int m = lane; m <= ci.Lt; m += GS) V[m] = cf[CF_G + m];
-      __syncwarp(gm);
-      for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
-        const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = lane; o < n; o += GS) vrr_bra<FOLD>(ld_op(kVrrOps, off + o), V, S, 1, c);
-        __syncwarp(gm);
-      }
-      for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
-        const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = lane; o < n; o += GS) vrr_ket<FOLD>(ld_op(kVrrOps, off + o), V, S, 1, c);
-        __syncwarp(gm);
-      }
-      for (int a = lane; a < ci.n_accl; a += GS) {
-        const uint32_t w = __ldg(kAccSrc + ci.acc_off + a);
-        S[w & 0xFFFF] += V[w >> 16];
-      }
-      __syncwarp(gm);
-    }
-    __syncwarp(gm);  // every lane is done with this chunk's coefficient sets
   }
   if (!any) return 0;
+  if (k > 1) {
+    for (int a = lane; a < nacc; a += 32) {
+      R sum = S[a];
+      for (int u = 1; u < k; ++u) sum += S[u * rsz + a];
+      S[a] = sum;
+    }
+    __syncwarp();
+  }
   if constexpr (sizeof(R) == 4) {
     // FP32 recurrences end at the contracted block: widen it to FP64 (through the free
     // coefficient area) so the horizontal recurrences and the spherical step, which cancel
     // across distant pairs, run in FP64 on the group's FP64 scratch
     double* Sd = reinterpret_cast<double*>(S);
     double* tmp = reinterpret_cast<double*>(CF);
-    for (int a = lane; a < ci.n_acc; a += GS) tmp[a] = (double)S[a];
-    __syncwarp(gm);
-    for (int a = lane; a < ci.n_acc; a += GS) Sd[a] = tmp[a];
-    __syncwarp(gm);
-    post_stages<double, GS>(ci, pa, bra, ket, Sd, lane, gm);
+    for (int a = lane; a < nacc; a += 32) tmp[a] = (double)S[a];
+    __syncwarp();
+    for (int a = lane; a < nacc; a += 32) Sd[a] = tmp[a];
+    __syncwarp();
+    post_stages<double>(ci, pa, bra, ket, Sd, lane);
   } else {
-    post_stages<R, GS>(ci, pa, bra, ket, S, lane, gm);
+    post_stages<R>(ci, pa, bra, ket, S, lane);
   }
   return any;
 }
@@ -166,7 +181,7 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const EriLau
 #define HFX_G1_MINB 6
 #endif
 #ifndef HFX_G32_MINB
-#define HFX_G32_MINB 6
+#define HFX_G32_MINB 8
 #endif
 // the batched thread-per-quartet kernel carries the batch bookkeeping too: 4 blocks per SM
 // keep it free of spills
@@ -203,56 +218,126 @@ struct Tally {
   unsigned long long prim = 0, quart = 0, skip = 0, q32 = 0, p32 = 0;
 };
 
-// Quartets [q0, q1) of the launch record Ls, G = 1: lane `lane` of the warp takes
-// q0 + lane, q0 + lane + 32, ... (neighbouring lanes on neighbouring quartets).  ci: the
-// launch's class record; the system fields used per quartet are copied to registers once
-// per range (Ls may live in global memory, where the K updates could alias it).
-__device__ __forceinline__ void g1_range(const EriClassInfo& ci, const EriLaunch& Ls, long long q0, long long q1,
-                                         double* S, int st, int lane, Tally& t) {
-  if (q0 + lane >= q1) return;
-  const long long* qoff = Ls.qoff;
-  const int* sorted = Ls.sorted;
-  const int* psa = Ls.pa.sa;
-  const int* psb = Ls.pa.sb;
-  const int* pn = Ls.pa.prim_n;
-  const int* bf_off = Ls.sh.bf_off;
-  const int row_begin = Ls.row_begin, bra0 = Ls.bra_bin_start, ket0 = Ls.ket_bin_start;
-  const bool skip = Ls.skip_zero;
-  const double dens = Ls.dens_tau;
-  const double* Qs = Ls.Qs;
-  const double* P = Ls.P;
-  double* K = Ls.K;
-  const int ld = Ls.ld;
-  int r = find_row(qoff, row_begin, Ls.row_end, q0 + lane);
-  for (long long q = q0 + lane; q < q1; q += 32) {
-    while (__ldg(qoff + r + 1) <= q) ++r;
-    const int bra_s = bra0 + (r - row_begin);
-    const int ket_s = ket0 + (int)(q - __ldg(qoff + r));
-    const int bra = __ldg(sorted + bra_s), ket = __ldg(sorted + ket_s);
-    const int sa = __ldg(psa + bra), sb = __ldg(psb + bra);
-    const int sc = __ldg(psa + ket), sd = __ldg(psb + ket);
-    const double pm = pmax4(Ls, sa, sb, sc, sd);
-    if (skip && pm == 0.0) continue;
-    if (dens > 0.0 && __ldg(Qs + bra_s) * __ldg(Qs + ket_s) * pm < dens) continue;
-    const int npq = __ldg(pn + bra) * __ldg(pn + ket);
-    const int ne = contract_g1(ci, Ls, bra, ket, S, st);
-    t.prim += ne;
-    t.skip += npq - ne;
-    if (!ne) continue;
-    ++t.quart;
-    double deg = 1.0;
-    if (sa == sb) deg *= 0.5;
-    if (sc == sd) deg *= 0.5;
-    if (bra_s == ket_s) deg *= 0.5;
-    digest(ci, S + ci.out_base * st, st, __ldg(bf_off + sa), __ldg(bf_off + sb), __ldg(bf_off + sc),
-           __ldg(bf_off + sd), deg, P, K, ld, 0, 1);
+// One quartet evaluated and digested by one lane (one quartet per thread).
+__device__ __forceinline__ void g1_quartet(const EriClassInfo& ci, const EriLaunch& Ls, int bra_s, int ket_s,
+                                           double* S, int st, Tally& t) {
+  const int bra = __ldg(Ls.sorted + bra_s), ket = __ldg(Ls.sorted + ket_s);
+  const int sa = __ldg(Ls.pa.sa + bra), sb = __ldg(Ls.pa.sb + bra);
+  const int sc = __ldg(Ls.pa.sa + ket), sd = __ldg(Ls.pa.sb + ket);
+  const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
+  const int ne = contract_g1(ci, Ls, bra, ket, S, st);
+  t.prim += ne;
+  t.skip += npq - ne;
+  if (!ne) return;
+  ++t.quart;
+  double deg = 1.0;
+  if (sa == sb) deg *= 0.5;
+  if (sc == sd) deg *= 0.5;
+  if (bra_s == ket_s) deg *= 0.5;
+  digest(ci, S + ci.out_base * st, st, __ldg(Ls.sh.bf_off + sa), __ldg(Ls.sh.bf_off + sb), __ldg(Ls.sh.bf_off + sc),
+         __ldg(Ls.sh.bf_off + sd), deg, Ls.P, Ls.K, Ls.ld, 0, 1);
+}
+
+// Per-warp queue of the quartets that pass the density tests (64 entries: system, bra
+// position, ket position, primitive quartets).  Lanes evaluate quartets 32 at a time, the
+// 32 with the most primitive quartets first, so that few lanes idle while the others
+// finish their primitive loops (the FP64 pipe charges a warp instruction in full whatever
+// the number of active lanes).
+struct G1Queue {
+  int4* q;
+  int n;
+};
+
+// Descending bitonic sort of 64 keys, two per lane (element i = lane + 32 h).
+__device__ __forceinline__ void sort64_desc(int& k0, int& k1, int lane) {
+#pragma unroll
+  for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      int o0, o1;
+      if (stride == 32) {
+        o0 = k1;
+        o1 = k0;
+      } else {
+        o0 = __shfl_xor_sync(0xffffffffu, k0, stride);
+        o1 = __shfl_xor_sync(0xffffffffu, k1, stride);
+      }
+      const int i0 = lane, i1 = lane + 32;
+      const int j0 = i0 ^ stride, j1 = i1 ^ stride;
+      const bool d0 = ((min(i0, j0) & size) == 0), d1 = ((min(i1, j1) & size) == 0);
+      const bool m0 = (i0 < j0) == d0, m1 = (i1 < j1) == d1;
+      k0 = m0 ? max(k0, o0) : min(k0, o0);
+      k1 = m1 ? max(k1, o1) : min(k1, o1);
+    }
   }
 }
 
-// Quartets [q0, q1) of the launch record Ls, G = 32: the warp takes them one by one.
-template <bool FOLD, bool MIXED, int GS>
-__device__ __forceinline__ void g32_range(const EriClassInfo& ci, const EriLaunch& Ls, long long q0, long long q1,
-                                          double* S, double* CF, int lane, unsigned gm, Tally& t) {
+template <bool BATCH>
+__device__ __forceinline__ void g1_drain(const EriLaunch& L, const EriClassInfo& ci, G1Queue& Q, int lane, double* S,
+                                         int st, Tally& t, bool all) {
+  while (Q.n >= 32 || (all && Q.n > 0)) {
+    int4 e;
+    int take;
+    if (Q.n >= 32) {
+      // the 32 entries with the most primitive quartets; the rest move to the front
+      int k0 = lane < Q.n ? ((Q.q[lane].w << 6) | lane) : -1;
+      int k1 = lane + 32 < Q.n ? ((Q.q[lane + 32].w << 6) | (lane + 32)) : -1;
+      sort64_desc(k0, k1, lane);
+      e = Q.q[k0 & 63];
+      int4 rest = make_int4(0, 0, 0, 0);
+      if (k1 >= 0) rest = Q.q[k1 & 63];
+      __syncwarp();
+      if (k1 >= 0) Q.q[lane] = rest;
+      take = 32;
+    } else {
+      e = Q.q[lane];
+      take = Q.n;
+    }
+    __syncwarp();
+    Q.n -= take;
+    if (lane < take) g1_quartet(ci, BATCH ? L.batch[e.x] : L, e.y, e.z, S, st, t);
+  }
+}
+
+// Quartets [q0, q1) of the launch record Ls (system sys), one quartet per thread: the warp
+// tests 32 consecutive quartets at a time and queues the survivors.
+template <bool BATCH>
+__device__ __forceinline__ void g1_range(const EriLaunch& L, const EriClassInfo& ci, const EriLaunch& Ls, int sys,
+                                         long long q0, long long q1, double* S, int st, int lane, G1Queue& Q,
+                                         Tally& t) {
+  const long long* qoff = Ls.qoff;
+  const int row_begin = Ls.row_begin, bra0 = Ls.bra_bin_start, ket0 = Ls.ket_bin_start;
+  const bool skip = Ls.skip_zero;
+  const double dens = Ls.dens_tau;
+  int r = -1;
+  for (long long base = q0; base < q1; base += 32) {
+    const long long q = base + lane;
+    bool keep = false;
+    int bra_s = 0, ket_s = 0, npq = 0;
+    if (q < q1) {
+      if (r < 0) r = find_row(qoff, row_begin, Ls.row_end, q);
+      while (__ldg(qoff + r + 1) <= q) ++r;
+      bra_s = bra0 + (r - row_begin);
+      ket_s = ket0 + (int)(q - __ldg(qoff + r));
+      const int bra = __ldg(Ls.sorted + bra_s), ket = __ldg(Ls.sorted + ket_s);
+      const double pm = pmax4(Ls, __ldg(Ls.pa.sa + bra), __ldg(Ls.pa.sb + bra), __ldg(Ls.pa.sa + ket),
+                              __ldg(Ls.pa.sb + ket));
+      keep = !(skip && pm == 0.0) && !(dens > 0.0 && __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pm < dens);
+      npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) Q.q[Q.n + __popc(m & ((1u << lane) - 1u))] = make_int4(sys, bra_s, ket_s, npq);
+    Q.n += __popc(m);
+    __syncwarp();
+    g1_drain<BATCH>(L, ci, Q, lane, S, st, t, false);
+  }
+}
+
+// Quartets [q0, q1) of the launch record Ls, one warp: the warp takes them one by one.
+// ci and sv: the launch's class record and schedule variant.
+template <bool MIXED>
+__device__ __forceinline__ void g32_range(const EriClassInfo& ci, const SchedVariant& sv, const EriLaunch& Ls,
+                                          long long q0, long long q1, double* S, double* CF, int lane, Tally& t) {
   float* Sf = reinterpret_cast<float*>(S);  // the FP32 engine reuses the group's memory
   float* CFf = reinterpret_cast<float*>(CF);
   if (q0 >= q1) return;
@@ -279,9 +364,9 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const EriLaunc
     const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
     int ne;
     if (MIXED && f32)
-      ne = contract_g32<float, FOLD, GS>(ci, Ls, bra, ket, Sf, CFf, lane, gm);
+      ne = contract_g32<float>(ci, sv, Ls, bra, ket, Sf, CFf, lane);
     else
-      ne = contract_g32<double, FOLD, GS>(ci, Ls, bra, ket, S, CF, lane, gm);
+      ne = contract_g32<double>(ci, sv, Ls, bra, ket, S, CF, lane);
     t.prim += ne;
     t.skip += npq - ne;
     if (!ne) continue;
@@ -297,8 +382,8 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const EriLaunc
     const int A = __ldg(Ls.sh.bf_off + sa), B = __ldg(Ls.sh.bf_off + sb);
     const int C = __ldg(Ls.sh.bf_off + sc), D = __ldg(Ls.sh.bf_off + sd);
     // an FP32 quartet leaves its final block in FP64 too (see contract_g32)
-    digest(ci, S + ci.out_base, 1, A, B, C, D, deg, Ls.P, Ls.K, Ls.ld, lane, GS);
-    __syncwarp(gm);
+    digest(ci, S + ci.out_base, 1, A, B, C, D, deg, Ls.P, Ls.K, Ls.ld, lane, 32);
+    __syncwarp();
   }
 }
 
@@ -312,7 +397,7 @@ __device__ __forceinline__ void for_each_range(const EriLaunch& L, long long wid
   if (!BATCH && L.schedule != 2) {
     long long q0, q1;
     group_range(L, wid, nw, q0, q1);
-    f(L, q0, q1);
+    f(L, 0, q0, q1);
     return;
   }
   const long long total = L.q_count;
@@ -324,7 +409,7 @@ __device__ __forceinline__ void for_each_range(const EriLaunch& L, long long wid
     if (c0 >= total) break;
     const long long c1 = min(c0 + L.chunk, total);
     if constexpr (!BATCH) {
-      f(L, L.q_begin + c0, L.q_begin + c1);
+      f(L, 0, L.q_begin + c0, L.q_begin + c1);
     } else {
       while (c0 < c1) {
         int lo = 0, hi = L.n_sys - 1;  // last s with seg[s] <= c0
@@ -334,7 +419,7 @@ __device__ __forceinline__ void for_each_range(const EriLaunch& L, long long wid
         }
         const long long e = min(c1, __ldg(L.seg + lo + 1));
         const EriLaunch& Ls = L.batch[lo];
-        f(Ls, Ls.q_begin + (c0 - __ldg(L.seg + lo)), Ls.q_begin + (e - __ldg(L.seg + lo)));
+        f(Ls, lo, Ls.q_begin + (c0 - __ldg(L.seg + lo)), Ls.q_begin + (e - __ldg(L.seg + lo)));
         c0 = e;
       }
     }
@@ -362,10 +447,12 @@ __global__ void __launch_bounds__(64, BATCH ? HFX_G1B_MINB : HFX_G1_MINB) eri_g1
   if (MODE == 0) {
     const int lane = threadIdx.x & 31;
     Tally t;
+    G1Queue Q{reinterpret_cast<int4*>(smem + (size_t)L.ci.scratch * blockDim.x) + (threadIdx.x >> 5) * 64, 0};
     for_each_range<BATCH, 32>(L, gid >> 5, ng >> 5, lane, 0xffffffffu,
-                          [&](const EriLaunch& Ls, long long q0, long long q1) {
-                            g1_range(L.ci, Ls, q0, q1, S, st, lane, t);
-                          });
+                              [&](const EriLaunch& Ls, int sys, long long q0, long long q1) {
+                                g1_range<BATCH>(L, L.ci, Ls, sys, q0, q1, S, st, lane, Q, t);
+                              });
+    g1_drain<BATCH>(L, L.ci, Q, lane, S, st, t, true);
     flush_tally(L, t);
   } else {
     for (long long t = gid; t < L.diag_n; t += ng) {
@@ -378,34 +465,31 @@ __global__ void __launch_bounds__(64, BATCH ? HFX_G1B_MINB : HFX_G1_MINB) eri_g1
   record_busy(L, t0);
 }
 
-template <int MODE, bool FOLD, bool MIXED, bool BATCH, int GS>
-__global__ void __launch_bounds__(64, MIXED ? HFX_G32M_MINB : HFX_G32_MINB) eri_g32_kernel(const EriLaunch L,
-                                                                                            int group_stride) {
-  static_assert(GS == 8 || GS == 16 || GS == 32, "group size");
-  static_assert(!MIXED || GS == 32, "the FP32 engine widens its block through 32 coefficient sets");
+template <int MODE, bool MIXED, bool BATCH>
+__global__ void __launch_bounds__(64, MIXED ? HFX_G32M_MINB : HFX_G32_MINB) eri_g32_kernel(const EriLaunch L) {
   extern __shared__ double smem[];
-  const int lane = threadIdx.x & (GS - 1), grp = threadIdx.x / GS;
-  const unsigned gm = GS == 32 ? 0xffffffffu : (((1u << GS) - 1u) << ((threadIdx.x & 31) & ~(GS - 1)));
-  const int gpb = blockDim.x / GS;
-  double* S = smem + grp * group_stride;
-  double* CF = S + L.ci.scratch + (L.ci.scratch & 1);
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int gpb = blockDim.x >> 5;
+  double* S = smem + grp * g32_stride(L.sv);
+  double* CF = S + L.sv.group;
   const long long gid = (long long)blockIdx.x * gpb + grp;
   const long long ng = (long long)gridDim.x * gpb;
   unsigned long long t0 = 0;
   if (L.busy && threadIdx.x == 0) t0 = globaltimer_ns();
   if (MODE == 0) {
     Tally t;
-    for_each_range<BATCH, GS>(L, gid, ng, lane, gm, [&](const EriLaunch& Ls, long long q0, long long q1) {
-      g32_range<FOLD, MIXED, GS>(L.ci, Ls, q0, q1, S, CF, lane, gm, t);
-    });
+    for_each_range<BATCH, 32>(L, gid, ng, lane, 0xffffffffu,
+                              [&](const EriLaunch& Ls, int, long long q0, long long q1) {
+                                g32_range<MIXED>(L.ci, L.sv, Ls, q0, q1, S, CF, lane, t);
+                              });
     if (lane == 0) flush_tally(L, t);
   } else {
     for (long long t = gid; t < L.diag_n; t += ng) {
       const int p = __ldg(L.diag_list + t);
       double mx = 0.0;
-      if (contract_g32<double, FOLD, GS>(L.ci, L, p, p, S, CF, lane, gm)) mx = diag_max(L.ci, S + L.ci.out_base, 1);
+      if (contract_g32<double>(L.ci, L.sv, L, p, p, S, CF, lane)) mx = diag_max(L.ci, S + L.ci.out_base, 1);
       if (lane == 0) L.diag_Q[p] = sqrt(mx);
-      __syncwarp(gm);
+      __syncwarp();
     }
   }
   record_busy(L, t0);
@@ -428,42 +512,62 @@ int eri_group_size(int cls) {
 // template parameter; only 32 is built.
 bool eri_group_size_valid(int gs) { return gs == 1 || gs == 32; }
 
-static int group_stride(int cls, int gs) {
-  const int s = kClassInfo[cls].scratch;
-  return s + (s & 1) + gs * NCOEF + 1;  // +1: stagger the groups' banks
+// Streams of the warp kernel per class (primitive quartets run at a time).  Defaults from a
+// sweep of k = 1, 2, 4 over every warp class of the 64-atom diamond build (plain FP64): more
+// streams fill the iterations with fewer FP64 warp instructions per primitive quartet, but
+// their larger group scratch lowers the resident warps, which the largest classes feel most.
+static const int kDefaultStreams[HFX_N_CLASSES] = {
+    4, 4, 4, 4, 4, 4,   // ss|ss ps|ss ps|ps pp|ss pp|ps pp|pp
+    4, 4, 4, 4,         // ds|ss ds|ps ds|pp ds|ds
+    4, 4, 2, 4, 2,      // dp|ss dp|ps dp|pp dp|ds dp|dp
+    4, 4, 2, 2, 1, 1};  // dd|ss dd|ps dd|pp dd|ds dd|dp dd|dd
+
+static int variant_index(int cls, int streams) {
+  const SchedVariant* v = kSchedInfo[cls];
+  if (streams > 0) {
+    for (int i = 0; i < 3; ++i)
+      if (v[i].k == streams) return i;
+    return -1;
+  }
+  int best = 0;  // the largest variant carried up to the default
+  for (int i = 1; i < 3; ++i)
+    if (v[i].k && v[i].k <= kDefaultStreams[cls]) best = i;
+  return best;
 }
 
-// classes whose tables fold the accumulation (the thread-per-quartet ones)
-static bool class_folds(int cls) { return kClassInfo[cls].scratch <= HFX_G1_MAX_SCRATCH; }
+bool eri_streams_valid(int cls, int streams) {
+  return cls >= 0 && cls < HFX_N_CLASSES && (streams == 0 || variant_index(cls, streams) >= 0);
+}
 
-template <int MODE, bool MIXED, bool BATCH, int GS>
-static const void* group_kernel(bool fold) {
-  return fold ? (const void*)eri_g32_kernel<MODE, true, MIXED, BATCH, GS>
-              : (const void*)eri_g32_kernel<MODE, false, MIXED, BATCH, GS>;
+int eri_streams(int cls, int streams) {
+  const int i = variant_index(cls, streams);
+  return i < 0 ? 0 : kSchedInfo[cls][i].k;
 }
 
 // The kernel instance for a class launch.  gs: lanes per quartet (1 = a thread, 32 = a warp);
 // mode 1 = Schwarz diagonal; batch = quartets of several systems in one launch.
-static const void* kernel_ptr(int cls, int mode, int gs, bool mixed, bool batch) {
-  const bool fold = class_folds(cls);
+static const void* kernel_ptr(int mode, int gs, bool mixed, bool batch) {
   if (gs == 1) {
     if (mode == 1) return (const void*)eri_g1_kernel<1, false>;
     return batch ? (const void*)eri_g1_kernel<0, true> : (const void*)eri_g1_kernel<0, false>;
   }
-  if (mode == 1) return group_kernel<1, false, false, 32>(fold);
-  if (mixed) return batch ? group_kernel<0, true, true, 32>(fold) : group_kernel<0, true, false, 32>(fold);
-  return batch ? group_kernel<0, false, true, 32>(fold) : group_kernel<0, false, false, 32>(fold);
+  if (mode == 1) return (const void*)eri_g32_kernel<1, false, false>;
+  if (mixed) return batch ? (const void*)eri_g32_kernel<0, true, true> : (const void*)eri_g32_kernel<0, true, false>;
+  return batch ? (const void*)eri_g32_kernel<0, false, true> : (const void*)eri_g32_kernel<0, false, false>;
 }
 
 // the group size a launch actually runs with
 static int effective_gs(int mode, int gs, bool mixed) {
   if (gs == 1) return 1;
-  return (mode == 1 || mixed || !eri_group_size_valid(gs)) ? 32 : gs;
+  return 32;
 }
 
-size_t eri_smem_bytes(int cls, int gs) {
-  if (gs == 1) return sizeof(double) * (size_t)kClassInfo[cls].scratch * kBlock;
-  return sizeof(double) * (size_t)group_stride(cls, gs) * (kBlock / gs);
+size_t eri_smem_bytes(int cls, int gs, int streams) {
+  // one quartet per thread: interleaved scratch, then a 64-entry quartet queue per warp
+  if (gs == 1) return sizeof(double) * (size_t)kClassInfo[cls].scratch * kBlock + sizeof(int4) * 64 * (kBlock / 32);
+  const int i = variant_index(cls, streams);
+  if (i < 0) return (size_t)1 << 30;
+  return sizeof(double) * (size_t)g32_stride(kSchedInfo[cls][i]) * (kBlock / 32);
 }
 
 int eri_block_size() { return kBlock; }
@@ -471,42 +575,44 @@ int eri_block_size() { return kBlock; }
 cudaError_t eri_prepare() {
   // allow the largest dynamic shared memory any class needs, for every instance
   size_t mx = 0;
-  for (int c = 0; c < HFX_N_CLASSES; ++c)
-    for (int gs : {1, 32}) mx = std::max(mx, eri_smem_bytes(c, gs));
+  for (int c = 0; c < HFX_N_CLASSES; ++c) {
+    mx = std::max(mx, eri_smem_bytes(c, 1, 0));
+    for (int i = 0; i < 3; ++i)
+      if (kSchedInfo[c][i].k) mx = std::max(mx, eri_smem_bytes(c, 32, kSchedInfo[c][i].k));
+  }
   if (mx > 227 * 1024) mx = 227 * 1024;
-  for (int cls : {0, HFX_N_CLASSES - 1})
-    for (int mode = 0; mode < 2; ++mode)
-      for (int gs : {1, 32})
-        for (int mixed = 0; mixed < 2; ++mixed)
-          for (int batch = 0; batch < 2; ++batch) {
-            cudaError_t e = cudaFuncSetAttribute(kernel_ptr(cls, mode, gs, mixed, batch),
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-            if (e != cudaSuccess) return e;
-          }
+  for (int mode = 0; mode < 2; ++mode)
+    for (int gs : {1, 32})
+      for (int mixed = 0; mixed < 2; ++mixed)
+        for (int batch = 0; batch < 2; ++batch) {
+          cudaError_t e = cudaFuncSetAttribute(kernel_ptr(mode, gs, mixed, batch),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+          if (e != cudaSuccess) return e;
+        }
   return cudaSuccess;
 }
 
-int eri_blocks_per_sm(int cls, int mode, int gs, bool mixed, bool batch) {
+int eri_blocks_per_sm(int cls, int mode, int gs, bool mixed, bool batch, int streams) {
   int n = 0;
   const int g = effective_gs(mode, gs, mixed);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(cls, mode, g, mixed, batch), kBlock,
-                                                    eri_smem_bytes(cls, g)) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(mode, g, mixed, batch), kBlock,
+                                                    eri_smem_bytes(cls, g, streams)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
 int eri_groups_per_block(int mode, int gs, bool mixed) { return kBlock / effective_gs(mode, gs, mixed); }
 
-cudaError_t eri_launch(const EriLaunch& L, int cls, int mode, int grid, cudaStream_t stream, int gs, bool mixed,
-                       bool batch) {
+cudaError_t eri_launch(const EriLaunch& L0, int cls, int mode, int grid, cudaStream_t stream, int gs, bool mixed,
+                       bool batch, int streams) {
   const int g = effective_gs(mode, gs, mixed);
-  const size_t smem = eri_smem_bytes(cls, g);
+  const size_t smem = eri_smem_bytes(cls, g, streams);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  const void* k = kernel_ptr(cls, mode, g, mixed, batch);
-  int stride = group_stride(cls, g);
-  void* args_g1[] = {(void*)&L};
-  void* args_grp[] = {(void*)&L, (void*)&stride};
-  return cudaLaunchKernel(k, dim3(grid), dim3(kBlock), g == 1 ? args_g1 : args_grp, smem, stream);
+  const void* k = kernel_ptr(mode, g, mixed, batch);
+  EriLaunch L = L0;
+  if (g == 32) L.sv = kSchedInfo[cls][variant_index(cls, streams)];
+  void* args[] = {(void*)&L};
+  return cudaLaunchKernel(k, dim3(grid), dim3(kBlock), args, smem, stream);
 }
 
 }  // namespace hfx

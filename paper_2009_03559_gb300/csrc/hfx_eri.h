@@ -11,15 +11,19 @@ struct EriLaunch;
 // Schwarz-diagonal launches run groups of 32 whatever gs > 1 is asked.
 int eri_group_size(int cls);  // default for a class: 1 or 32
 bool eri_group_size_valid(int gs);
-size_t eri_smem_bytes(int cls, int gs);
+size_t eri_smem_bytes(int cls, int gs, int streams = 0);
 int eri_block_size();
 cudaError_t eri_prepare();
-int eri_blocks_per_sm(int cls, int mode, int gs, bool mixed, bool batch);
+int eri_blocks_per_sm(int cls, int mode, int gs, bool mixed, bool batch, int streams = 0);
+// Streams of the warp kernel (primitive quartets run at a time): 0 = the class default;
+// the value a launch with `streams` uses; whether a class has that variant.
+int eri_streams(int cls, int streams);
+bool eri_streams_valid(int cls, int streams);
 int eri_groups_per_block(int mode, int gs, bool mixed);
 
 }  // namespace hfx
 
 namespace hfx {
 cudaError_t eri_launch(const EriLaunch& L, int cls, int mode, int grid, cudaStream_t stream, int gs, bool mixed,
-                       bool batch);
+                       bool batch, int streams = 0);
 }

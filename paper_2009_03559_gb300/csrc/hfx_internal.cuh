@@ -28,15 +28,22 @@ struct EriClassInfo {
 extern const EriClassInfo* class_info_host();
 
 // ---------------------------------------------------------------------------
-// Boys function table: rows at x_g = g h, column 0 = exp(-x_g), columns 1..16 =
-// F_0..F_15 at x_g (F_m(x) = int_0^1 u^{2m} exp(-x u^2) du).
+// Boys function tables, one per order L = 0..kMaxLt, rows at x_g = g h (h = 1/32,
+// g = 0..kBoysRows-1).  Row g of table L holds the coefficients of the Taylor expansions
+// about x_g in powers of d = x - x_g:
+//   [0] x_g,  [1 + k] (-1)^k F_{L+k}(x_g) / k!,  [8 + k] (-1)^k exp(-x_g) / k!  (k = 0..6),
+//   [15] 0,
+// with F_m(x) = int_0^1 u^{2m} exp(-x u^2) du.  Seven terms with |d| <= h/2 leave a
+// relative error below 5e-17.
 // ---------------------------------------------------------------------------
-constexpr int kBoysCols = 17;
-constexpr double kBoysInvStep = 32.0;
+constexpr int kBoysRowLen = 16;
+constexpr float kBoysInvStepF = 32.0f;
 constexpr double kBoysStep = 1.0 / 32.0;
 constexpr double kBoysXmax = 60.0;
+constexpr int kBoysXmaxHi = 0x404E0000;   // high word of 60.0 (low word 0)
 constexpr int kBoysRows = 60 * 32 + 2;
 constexpr int kMaxLt = 8;
+constexpr int kBoysTableLen = kBoysRows * kBoysRowLen;   // doubles per order
 
 // ---------------------------------------------------------------------------
 // Primitive-pair record (one per surviving primitive pair of a shell pair).
@@ -48,9 +55,9 @@ struct __align__(16) PrimPair {
   double P[3];         // Gaussian product centre
   double PA[3];        // P - A (A = centre of the pair's first shell)
   double C;            // prefactor (see above)
-  double pad;
-  // FP32 copies for the FP32 recurrences (conversions would run on the FP64 pipe)
-  float pf, inv2pf, PAf[3], pad_f[3];
+  double inv2p3;       // 3/(2p)
+  // FP32 copies for the FP32 recurrences
+  float pf, inv2pf, PAf[3], Pf[3];
 };
 
 // Device arrays describing shell pairs (indexed by candidate-pair id).
@@ -69,77 +76,78 @@ struct ShellArrays {
 };
 
 // ---------------------------------------------------------------------------
-// FP64 reciprocal and reciprocal square root: FP32 hardware seed (relative error below
-// 2^-22) refined by one Newton-Raphson step, which squares the error: below 1e-13
-// relative, far inside what the exchange matrix needs (FP64 instructions are the scarce
-// resource on this part).  Arguments are positive and well inside FP32 range.
+// Conversions and reciprocals that keep the FP64 pipe free.  On this part the FP64 pipe
+// executes one warp instruction every 16 SM cycles whatever the number of active lanes,
+// while integer, FP32 and special-function units are some 64 times wider, so the FP32 seeds
+// of reciprocals are made from the bit patterns of the doubles.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double rcp_nr(double x) {
-  const double r = (double)__frcp_rn((float)x);
-  return fma(r, fma(-x, r, 1.0), r);
+// FP32 value of a double x in [2^-126, 2^128) by truncation of the mantissa (0 below).
+__device__ __forceinline__ float approx_f32(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int fb = (int)(((unsigned)(hi - (896 << 20)) << 3) | (lo >> 29));
+  return __int_as_float(hi < (897 << 20) ? 0 : fb);
 }
+// Double with the value 2^e2 * f of a positive normal float f (e2 = 0 or -1): exact.
+__device__ __forceinline__ double widen_f32(float f, int e2 = 0) {
+  const int fb = __float_as_int(f);
+  return __hiloint2double((fb >> 3) + ((896 + e2) << 20), fb << 29);
+}
+// 2^e x for a positive normal double x (exact; e small).
+__device__ __forceinline__ double scale2(double x, int e) {
+  return __hiloint2double(__double2hiint(x) + (e << 20), __double2loint(x));
+}
+// x >= 2^e... comparisons of non-negative doubles on the high word (integer units).
+__device__ __forceinline__ bool ge_hi(double x, int hi) { return __double2hiint(x) >= hi; }
 
+// 1/sqrt(x) for x > 0 in FP32 range: FP32 hardware seed (relative error below 2^-22),
+// one Newton-Raphson step (the error squares: below 1e-13 relative).  3 FP64 instructions.
 __device__ __forceinline__ double rsqrt_nr(double x) {
-  const double y = (double)rsqrtf((float)x);
-  return fma(0.5 * y, fma(-x * y, y, 1.0), y);  // y (1 + (1 - x y^2)/2)
+  const float yf = rsqrtf(approx_f32(x));
+  const double y = widen_f32(yf);
+  const double hy = widen_f32(yf, -1);            // y / 2
+  const double r = fma(-x * y, y, 1.0);           // 1 - x y^2
+  return fma(hy, r, y);
 }
 
-// F_m(x) for m = 0..mmax (mmax <= kMaxLt).  Below kBoysXmax: seven-term Taylor
-// expansion of F_mmax and exp(-x) about the nearest grid point (|x - x_g| <= h/2),
-// then downward recursion F_{m-1} = (2x F_m + e^{-x}) / (2m-1); for mmax <= 1 every
-// order is expanded directly.  Above: F_0 = sqrt(pi/x)/2 and F_{m+1} = (m+1/2) F_m / x
-// (the neglected terms are below exp(-60) relative to F_m for m <= 8).
-__device__ __forceinline__ void boys_eval(int mmax, double x, const double* __restrict__ tab,
-                                          double* F) {
-  if (x < kBoysXmax) {
-    int g = __double2int_rn(x * kBoysInvStep);
-    double md = fma(-kBoysStep, (double)g, x);  // x - x_g
-    md = -md;
-    const double* row = tab + g * kBoysCols;
-    double d2 = md * 0.5, d3 = md * (1.0 / 3.0), d4 = md * 0.25, d5 = md * 0.2, d6 = md * (1.0 / 6.0);
-    if (mmax <= 1) {
-      for (int m = 0; m <= mmax; ++m) {
-        const double* f = row + 1 + m;
-        double r = f[6];
-        r = fma(r, d6, f[5]);
-        r = fma(r, d5, f[4]);
-        r = fma(r, d4, f[3]);
-        r = fma(r, d3, f[2]);
-        r = fma(r, d2, f[1]);
-        F[m] = fma(r, md, f[0]);
-      }
-      return;
-    }
-    const double* f = row + 1 + mmax;
-    double r = f[6];
-    r = fma(r, d6, f[5]);
-    r = fma(r, d5, f[4]);
-    r = fma(r, d4, f[3]);
-    r = fma(r, d3, f[2]);
-    r = fma(r, d2, f[1]);
-    F[mmax] = fma(r, md, f[0]);
-    double e = fma(d6, 1.0, 1.0);
-    e = fma(e, d5, 1.0);
-    e = fma(e, d4, 1.0);
-    e = fma(e, d3, 1.0);
-    e = fma(e, d2, 1.0);
-    e = fma(e, md, 1.0);
-    e *= row[0];
-    double x2 = x + x;
+// F_L(x) and exp(-x) for 0 <= x < kBoysXmax from the table of order L (13 FP64
+// instructions: the offset from the grid point and two Horner chains).
+__device__ __forceinline__ void boys_top(double x, const double* __restrict__ tabL, double& F, double& e) {
+  const int g = __float2int_rn(approx_f32(x) * kBoysInvStepF);
+  const double2* row = reinterpret_cast<const double2*>(tabL + g * kBoysRowLen);
+  const double2 r0 = __ldg(row), r1 = __ldg(row + 1), r2 = __ldg(row + 2), r3 = __ldg(row + 3);
+  const double2 r4 = __ldg(row + 4), r5 = __ldg(row + 5), r6 = __ldg(row + 6), r7 = __ldg(row + 7);
+  const double d = x - r0.x;
+  F = fma(fma(fma(fma(fma(fma(r3.y, d, r3.x), d, r2.y), d, r2.x), d, r1.y), d, r1.x), d, r0.y);
+  e = fma(fma(fma(fma(fma(fma(r7.x, d, r6.y), d, r6.x), d, r5.y), d, r5.x), d, r4.y), d, r4.x);
+}
+
+// F_L(x) for x >= kBoysXmax: (2L-1)!!/2^{L+1} sqrt(pi) x^{-L-1/2} (the neglected terms are
+// below exp(-60) relative); exp(-x) is taken as 0.
+__device__ __forceinline__ double boys_asym(int L, double x) {
+  const double y = rsqrt_nr(x);
+  const double y2 = y * y;
+  double v = y;
+  double c = 0.886226925452758014;  // sqrt(pi)/2
 #pragma unroll
-    for (int m = kMaxLt; m >= 1; --m) {
-      if (m <= mmax) F[m - 1] = fma(x2, F[m], e) * (1.0 / (2 * m - 1));
-    }
-  } else {
-    double ix = rcp_nr(x);
-    double f0 = 0.886226925452758014 * rsqrt_nr(x);  // sqrt(pi)/2 / sqrt(x)
-    F[0] = f0;
-#pragma unroll
-    for (int m = 0; m < kMaxLt; ++m) {
-      if (m < mmax) F[m + 1] = F[m] * ((m + 0.5) * ix);
+  for (int m = 0; m < kMaxLt; ++m) {
+    if (m < L) {
+      v *= y2;
+      c *= (m + 0.5);
     }
   }
+  return c * v;
 }
+
+// Schedule variant of a class for the warp kernel (generated; see gen_eri_tables.py).
+struct SchedVariant {
+  int k;       // primitive quartets run at a time (streams), 0 = variant absent
+  int rsz;     // doubles (or floats) of group scratch per stream
+  int zero;    // index of the zero slot in a stream's region
+  int n_iter;  // iterations of 32 entries
+  int off;     // first entry in kSched (uint4 units)
+  int group;   // doubles of the stream regions together, at least the post-contraction scratch
+};
 
 // Arguments of one class launch (passed by value).
 struct EriLaunch {
@@ -154,8 +162,9 @@ struct EriLaunch {
   int schedule;               // 0 quartet split, 1 bra-pair split, 2 dynamic chunks
   unsigned long long* work;   // schedule 2: next unclaimed quartet (relative to q_begin)
   int chunk;                  // schedule 2: quartets per claim
-  const double* boys;
-  double omega2;
+  const double* boys;         // kMaxLt + 1 tables of kBoysTableLen doubles
+  double omega, omega2;
+  SchedVariant sv;             // warp kernel: the schedule variant of this class
   const double* P;
   double* K;
   int ld;

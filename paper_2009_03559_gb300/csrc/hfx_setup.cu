@@ -34,14 +34,15 @@ __global__ void k_normalize(int n_shells, const int* __restrict__ l, const int* 
 }
 
 // ---------------------------------------------------------------------------
-// Boys table: F_15(x_g) from its series exp(-x) sum_k (2x)^k / ((31)(33)...(31+2k)),
-// lower orders by the downward recursion F_{m-1} = (2x F_m + e^{-x}) / (2m-1).
+// Boys tables: at x_g = g h, F_15(x_g) from its series exp(-x) sum_k (2x)^k / ((31)(33)...(31+2k)),
+// lower orders by the downward recursion F_{m-1} = (2x F_m + e^{-x}) / (2m-1); then for every
+// order L = 0..kMaxLt the row of Taylor coefficients [x_g, (-1)^k F_{L+k}/k!, (-1)^k e^{-x_g}/k!].
 // ---------------------------------------------------------------------------
 __global__ void k_boys_table(double* __restrict__ tab) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= kBoysRows) return;
   const double x = g * kBoysStep;
-  const int M = kBoysCols - 2;
+  const int M = 15;
   double term = 1.0 / (2 * M + 1), sum = term;
   for (int k = 1; k < 4000; ++k) {
     term *= 2.0 * x / (2 * M + 2 * k + 1);
@@ -49,13 +50,19 @@ __global__ void k_boys_table(double* __restrict__ tab) {
     if (term < 1e-18 * sum) break;
   }
   const double e = exp(-x);
-  double F = e * sum;
-  double* row = tab + (size_t)g * kBoysCols;
-  row[0] = e;
-  row[1 + M] = F;
-  for (int m = M; m >= 1; --m) {
-    F = (2.0 * x * F + e) / (2 * m - 1);
-    row[m] = F;
+  double Fm[M + 1];
+  Fm[M] = e * sum;
+  for (int m = M; m >= 1; --m) Fm[m - 1] = (2.0 * x * Fm[m] + e) / (2 * m - 1);
+  const double inv_fact[7] = {1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720};
+  for (int L = 0; L <= kMaxLt; ++L) {
+    double* row = tab + (size_t)L * kBoysTableLen + (size_t)g * kBoysRowLen;
+    row[0] = x;
+    for (int k = 0; k < 7; ++k) {
+      const double sg = (k & 1) ? -inv_fact[k] : inv_fact[k];
+      row[1 + k] = sg * Fm[L + k];
+      row[8 + k] = sg * e;
+    }
+    row[15] = 0.0;
   }
 }
 
@@ -137,12 +144,12 @@ __global__ void k_prim_fill(int n_cand, const int* __restrict__ sa, const int* _
         r.PA[i] = r.P[i] - A[i];
       }
       r.C = C;
-      r.pad = 0.0;
+      r.inv2p3 = 1.5 / p;
       r.pf = (float)p;
       r.inv2pf = (float)r.inv2p;
       for (int i = 0; i < 3; ++i) {
         r.PAf[i] = (float)r.PA[i];
-        r.pad_f[i] = 0.f;
+        r.Pf[i] = (float)r.P[i];
       }
       out[n++] = r;
     }

@@ -74,7 +74,9 @@ class Stats(ctypes.Structure):
                 ("flops_fp64", ctypes.c_double), ("flops_class", ctypes.c_double * 21),
                 ("group_size_class", ctypes.c_int32 * 21),
                 ("ms_pairs", ctypes.c_double), ("ms_build", ctypes.c_double),
-                ("ms_class", ctypes.c_double * 21), ("energy", ctypes.c_double)]
+                ("ms_class", ctypes.c_double * 21), ("energy", ctypes.c_double),
+                ("flops_recurrence", ctypes.c_double), ("special_evals", ctypes.c_double),
+                ("streams_class", ctypes.c_int32 * 21), ("reserved_stats", ctypes.c_int32 * 1)]
 
     def as_dict(self):
         return {
@@ -88,6 +90,8 @@ class Stats(ctypes.Structure):
             "group_size_class": [int(x) for x in self.group_size_class], "ms_pairs": float(self.ms_pairs),
             "ms_build": float(self.ms_build), "ms_class": [float(x) for x in self.ms_class],
             "energy": float(self.energy),
+            "flops_recurrence": float(self.flops_recurrence), "special_evals": float(self.special_evals),
+            "streams_class": [int(x) for x in self.streams_class],
         }
 
 
@@ -135,6 +139,8 @@ def load_library(path: str = LIB_PATH):
     L.hfx_get_stats.restype = ctypes.c_int
     L.hfx_set_group_size.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.hfx_set_group_size.restype = ctypes.c_int
+    L.hfx_set_streams.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.hfx_set_streams.restype = ctypes.c_int
     L.hfx_set_timing.argtypes = [vp, ctypes.c_int]
     L.hfx_set_timing.restype = ctypes.c_int
     L.hfx_n_basis.argtypes = [vp]
@@ -300,6 +306,10 @@ class HFX:
     def set_group_size(self, cls, gs):
         """Lanes per quartet for quartet class cls in later builds (0 = default)."""
         self._check(self.L.hfx_set_group_size(self.h, int(cls), int(gs)))
+
+    def set_streams(self, cls, k):
+        """Primitive quartets the warp kernel runs at a time for class cls (0 = default)."""
+        self._check(self.L.hfx_set_streams(self.h, int(cls), int(k)))
 
     def set_timing(self, on=True):
         self._check(self.L.hfx_set_timing(self.h, 1 if on else 0))
