@@ -43,12 +43,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "HFX K-build ms & screened ERI quartets/s vs plain FP64; p50/p99 latency"
-# DRAM bytes (read + write) per launch of the warp-group ERI kernel on the 64-atom workload:
-# ncu dram__bytes_read.sum + dram__bytes_write.sum over its 48 class launches of four builds
-# (798.66 MB), taken on the current kernel version (with the density-screening test).
-G32_DRAM_BYTES_PER_LAUNCH = 798.66e6 / 48
-MASK_DESC = {"default": "13 classes with warp-group kernels, not (dd|dd)", "sp": "s,p classes only",
-             "all": "all classes"}
+MASK_DESC = {"default": "every class but (dd|dd)", "sp": "s,p classes only", "all": "all classes"}
 
 
 def class_mask(hfx, name):
@@ -57,7 +52,7 @@ def class_mask(hfx, name):
 
 def workload_desc(s, mixed=False, fp32_classes="default"):
     prec = ("mixed precision (FP32 recurrences where Q*Q*max|P| < 1e-6, "
-            f"{MASK_DESC[fp32_classes]}; FP64 Boys, HRR and K)" if mixed else "plain FP64")
+            f"{MASK_DESC[fp32_classes]}; FP64 Boys step, HRR, spherical step and K)" if mixed else "plain FP64")
     return (f"diamond-{s.n_atoms} DZP-like: {s.n_atoms} atoms (a=10.26 bohr cells), {s.n_shells} shells "
             f"s,s,p,p,d, {s.n_bf} spherical functions, 3 primitives/shell, omega=0.11, r_c=6 bohr, "
             f"tau=1e-8, P truncated beyond 10 bohr; {prec}")
@@ -441,6 +436,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--fp32-classes", default="default", choices=["default", "all", "sp"])
     ap.add_argument("--fp32-tau", type=float, default=1e-6)
+    ap.add_argument("--no-mixed", action="store_true", help="skip the same-run mixed-precision build")
+    ap.add_argument("--mixed-steps", type=int, default=5, help="timed mixed-precision builds in the main run")
     ap.add_argument("--density-tau", type=float, default=0.0,
                     help="density-weighted screening threshold (0 = off, the benchmark setting)")
     args = ap.parse_args()
@@ -478,44 +475,69 @@ def main():
                 fp32_class_mask=class_mask(hfx, args.fp32_classes),
                 fp32_tau=args.fp32_tau, density_tau=args.density_tau)
     h.build_pairs()
+    ms_pairs = h.stats()["ms_pairs"]
     P = torch.from_numpy(P_np).cuda()
     K = torch.empty_like(P)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     n_q = h.stats()["n_quartets"]
     fp64_peak, fp32_peak = hfx.measure_fma_peak()
 
-    # untimed warm-up; per-class CUDA events (on the library's stream) and counters stay on
-    # through the timed steps: they time the dominant kernel for the roofline
-    h.set_timing(True)
-    with torch.cuda.stream(stream):
-        for i in range(args.warmup):
-            h.build_K(P, K)
-    torch.cuda.synchronize()
+    def timed_builds(hh, KK, steps, warmup, sampler=None):
+        """warm-up, then `steps` builds each bracketed by CUDA events on the library's
+        stream (L2 flushed before each); per-class CUDA events and counters stay on"""
+        hh.set_timing(True)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                hh.build_K(P, KK)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if sampler:
+            sampler.start()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        cms, st = [], None
+        with torch.cuda.stream(stream):
+            for i in range(steps):
+                flush.fill_(float(i))
+                evs[i][0].record(stream)
+                hh.build_K(P, KK)
+                evs[i][1].record(stream)
+                st = hh.stats()  # waits for this step (outside its events)
+                cms.append(st["ms_class"])
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        ck = sampler.stop() if sampler else None
+        return [a.elapsed_time(b) for a, b in evs], cms, st, ck
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
-    clocks.start()
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
-    class_ms = []
-    with torch.cuda.stream(stream):
-        for i in range(args.steps):
-            flush.fill_(float(i))
-            ev[i][0].record(stream)
-            h.build_K(P, K)
-            ev[i][1].record(stream)
-            st_timed = h.stats()  # waits for this step (outside its events)
-            class_ms.append(st_timed["ms_class"])
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    ck = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    step_ms, class_ms, st_timed, ck = timed_builds(h, K, args.steps, args.warmup, clocks)
     total_ms = sum(step_ms)
     if pg:
         total_ms = max_over_ranks(total_ms, pg)
     energy = h.energy()
+
+    # the mixed-precision build of the same workload in the same run (the metric's
+    # comparison against plain FP64): time, throughput and errors against the FP64 K
+    mixed_obj = None
+    if not mixed and not args.no_mixed:
+        hm = hfx.HFX(s, stream=stream, precision=hfx.HFX_MIXED, fp32_tau=args.fp32_tau).build_pairs()
+        Km = torch.empty_like(P)
+        m_ms, _, st_m, _ = timed_builds(hm, Km, args.mixed_steps, 2)
+        d = (Km - K).abs()
+        m_med = float(np.median(m_ms))
+        mixed_obj = {
+            "ms_per_step": float(np.mean(m_ms)), "p50_ms": m_med, "p99_ms": float(np.percentile(m_ms, 99)),
+            "steps": args.mixed_steps, "quartets_per_s": n_q / (np.mean(m_ms) * 1e-3),
+            "speedup_vs_fp64": (total_ms / args.steps) / float(np.mean(m_ms)),
+            "quartets_fp32": int(sum(st_m["quartets_fp32_class"])),
+            "quartets_evaluated": int(sum(st_m["quartets_evaluated_class"])),
+            "max_abs_dK_vs_fp64": d.max().item(), "rms_dK_vs_fp64": float(torch.sqrt((d * d).mean()).item()),
+            "abs_dE_vs_fp64": abs(hm.energy() - energy), "fp32_tau": args.fp32_tau,
+            "fp32_classes": MASK_DESC["default"],
+        }
+        hm.close()
 
     # end-to-end through the host-buffer entry point (copies inside the timed region)
     e2e_t = []
@@ -525,20 +547,27 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
     nbytes = 8 * s.n_bf * s.n_bf
 
-    # roofline of the dominant kernel: the warp-cooperative FP64 kernel (classes with G=32)
+    # roofline of the dominant kernel: the warp-group kernel (the classes it runs), from the
+    # CUDA events around each class launch over the timed steps
     from paper_2009_03559_gb300.hfx import QUARTET_CLASSES
     ms_cls = [float(np.mean([c[k] for c in class_ms])) for k in range(21)]
     g32 = [c for c in range(21) if st_timed["group_size_class"][c] == 32]
-    flops_cls = st_timed["flops_class"]
     dom_ms = sum(ms_cls[c] for c in g32)
-    dom_fl = sum(flops_cls[c] for c in g32)
-    # mixed precision: the FP32 flops (all in warp-group classes) are weighted by the FP32 /
-    # FP64 peak ratio, so that frac = (F64/peak64 + F32/peak32) / time
+    prim_c = st_timed["prim_quartets_class"]
+    # algorithmic flops: vertical recurrence + contraction per primitive quartet, horizontal
+    # recurrence + spherical step + digest per quartet (the Boys evaluations are counted
+    # apart, as special-function evaluations)
+    rec_fl = sum(st_timed["flops_recurrence_class"][c] for c in g32)
+    set_fl = sum(st_timed["flops_class"][c] for c in g32)   # the same plus the primitive set-up
     f32 = st_timed["flops_fp32"] if mixed else 0.0
-    equiv = (dom_fl - f32) + f32 * (fp64_peak / fp32_peak)
-    achieved = equiv / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else None
-    # class launches + density-block maxima + K = A + A^T + two E_K reduction kernels
-    launches_per_step = sum(1 for c in range(21) if st_timed["n_quartets_class"][c] > 0) + 4
+    ach = lambda fl: (fl - f32 + f32 * (fp64_peak / fp32_peak)) / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else None
+    achieved, achieved_all = ach(rec_fl), ach(set_fl)
+    boys_per_s = sum(prim_c[c] * (2 if s.omega > 0 else 1) for c in g32) / (dom_ms * 1e-3) if dom_ms > 0 else None
+    # kernel launches per step: class launches (two per class taking FP32 under mixed precision)
+    # + density-block maxima + K = A + A^T + two E_K reduction kernels
+    n_cls = sum(1 for c in range(21) if st_timed["n_quartets_class"][c] > 0)
+    launches_per_step = n_cls + (sum(1 for c in range(21) if st_timed["n_quartets_class"][c] > 0 and
+                                     (hfx.FP32_CLASSES_DEFAULT >> c) & 1) if mixed else 0) + 4
 
     if rank == 0:
         line = {
@@ -556,20 +585,29 @@ def main():
                        "n_bf": s.n_bf, "quartets_per_step": n_q,
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{ws}",
                        "energy_E_K": energy},
+            "pair_build_ms": ms_pairs,
             "e2e": {"value": n_q / float(np.median(e2e_t)) if e2e_t else None, "unit": "quartets/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches_per_step * args.steps,
-            "roofline": {"bound": "alu", "kernel": "eri_g32_kernel (classes with warp groups), "
-                                                   "CUDA events around each class launch over the timed steps"
-                                                   + ("; FP32 flops counted at the FP64/FP32 peak ratio" if mixed else ""),
+            "roofline": {"bound": "alu", "kernel": "eri_g32_kernel (the classes run one quartet per warp), CUDA "
+                                                   "events around each class launch over the timed steps",
                          "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": (achieved / fp64_peak) if achieved else None,
-                         "traffic": G32_DRAM_BYTES_PER_LAUNCH if (args.atoms == 64 and not mixed) else None,
-                         "traffic_unit": "bytes per launch (ncu dram read + write)",
-                         "peak_source": "FP64 FMA-chain probe of this run (hfx_measure_fma_peak)"},
+                         "flops": "vertical recurrence + contraction per evaluated primitive quartet, horizontal "
+                                  "recurrence + spherical step + digest per evaluated quartet (operation counts "
+                                  "of the generated tables); Boys evaluations counted apart"
+                                  + ("; FP32 flops counted at the FP64/FP32 peak ratio" if mixed else ""),
+                         "traffic": None,
+                         "traffic_note": "not taken in this run (DRAM traffic of this kernel: profiles/)",
+                         "peak_source": "FP64 FMA-chain probe of this run (hfx_measure_fma_peak)",
+                         "with_setup": {"achieved": achieved_all, "frac": (achieved_all / fp64_peak) if achieved_all
+                                        else None, "flops": "the same plus the primitive set-up as written "
+                                                            "(Boys Taylor chains included)"},
+                         "boys_evals_per_s": boys_per_s},
             "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"]},
             "fp64_flops_per_step": st_timed["flops_fp64"],
             "fp32_flops_per_step": st_timed["flops_fp32"],
+            "recurrence_flops_per_step": st_timed["flops_recurrence"],
             "quartets_evaluated_per_step": sum(st_timed["quartets_evaluated_class"]),
             # class mixes compare on these: primitive quartets and spherical integrals per second
             "prim_quartets_per_s": sum(st_timed["prim_quartets_class"]) / (total_ms / args.steps * 1e-3),
@@ -580,15 +618,17 @@ def main():
             "fp32_peak_tflops": fp32_peak,
             "class_ms": {QUARTET_CLASSES[c]: round(ms_cls[c], 3) for c in range(21)},
         }
+        if mixed_obj:
+            line["mixed"] = mixed_obj
         if args.report:
-            print(f"{'class':9s} {'G':>2s} {'quartets':>11s} {'prims':>12s} {'ms':>9s} {'TF/s':>6s} {'frac':>5s}",
-                  file=sys.stderr)
+            print(f"{'class':9s} {'G':>2s} {'k':>2s} {'quartets':>11s} {'prims':>12s} {'ms':>9s} {'TF/s':>6s} "
+                  f"{'frac':>5s}", file=sys.stderr)
             for c in range(21):
                 ms = ms_cls[c]
-                fl = flops_cls[c]
+                fl = st_timed["flops_recurrence_class"][c]
                 tf = fl / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
-                print(f"{QUARTET_CLASSES[c]:9s} {st_timed['group_size_class'][c]:2d} "
-                      f"{st_timed['n_quartets_class'][c]:11d} {st_timed['prim_quartets_class'][c]:12d} "
+                print(f"{QUARTET_CLASSES[c]:9s} {st_timed['group_size_class'][c]:2d} {st_timed['streams_class'][c]:2d} "
+                      f"{st_timed['n_quartets_class'][c]:11d} {prim_c[c]:12d} "
                       f"{ms:9.2f} {tf:6.3f} {tf / fp64_peak:5.2f}", file=sys.stderr)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args)

@@ -56,13 +56,11 @@ extern "C" {
 #define HFX_FP64 0                /* every integral in FP64 */
 #define HFX_MIXED 1               /* FP32 recurrences for small-bound quartets, see hfx_options */
 
-/* Default classes allowed FP32 recurrences under HFX_MIXED: (pp|ps), (pp|pp), (ds|pp),
- * (ds|ds), (dp|ps), (dp|pp), (dp|ds), (dp|dp), (dd|ss), (dd|ps), (dd|pp), (dd|ds), (dd|dp).
- * Left in FP64: the seven classes whose FP64 kernel runs one quartet per thread (FP32 runs
- * one quartet per warp and was slower there), and (dd|dd), the highest recurrence
- * (L = 8): on the 64-atom diamond its FP32 recurrences alone moved E_K by 1.1e-7, while
- * each other class moved it by at most 2e-9. */
-#define HFX_FP32_CLASSES_DEFAULT 0xFFB30
+/* Default classes allowed FP32 recurrences under HFX_MIXED: every class but (dd|dd), the
+ * highest recurrence (L = 8): with FP32 there, E_K of the 64-atom diamond moved by 1.7e-7 and
+ * of the 216-atom one by 4.1e-7 (over the 1e-7 tolerance), against at most 1.1e-9 with the
+ * other twenty classes in FP32. */
+#define HFX_FP32_CLASSES_DEFAULT 0xFFFFF
 
 /* work schedules inside a class launch (paper Sec. 3.2, Algorithms 2 and 3) */
 #define HFX_SCHED_QUARTET 0       /* static even split of the screened quartet list */
@@ -80,7 +78,8 @@ typedef struct {
   double fp32_tau;     /* HFX_MIXED: a quartet's primitive recurrences (VRR) and their contraction
                           run in FP32 iff Q_IJ Q_KL Pmax < fp32_tau (default 1e-6), Pmax as set
                           by fp32_pmax_global; the Boys step, HRR, spherical step and all K
-                          accumulation stay FP64 */
+                          accumulation stay FP64.  The warp kernel runs FP32 quartets packed,
+                          two primitive quartets per float2 slot (FFMA2) */
   int precision;       /* HFX_FP64 (default) or HFX_MIXED */
   int schedule;        /* HFX_SCHED_DYNAMIC (default), HFX_SCHED_QUARTET or HFX_SCHED_PAIR */
   int skip_zero_p;     /* 1 (default): skip quartets whose four density blocks P_bd, P_bc,
@@ -125,6 +124,7 @@ typedef struct {
                                   primitive quartet with the erfc kernel, one with omega = 0 */
   int32_t streams_class[21];   /* warp kernel: primitive quartets run at a time per class */
   int32_t reserved_stats[1];
+  double flops_recurrence_class[21]; /* flops_recurrence per class */
 } hfx_stats;
 
 /* Primitive quartets the warp kernel runs at a time for quartet class cls (0..20) in later
@@ -227,9 +227,11 @@ void hfx_free(hfx_ctx* ctx);
 
 /* ---------------------------------------------------------------------------
  * Batched K builds: the quartets of several systems (contexts with pair lists) go into
- * one launch per angular class; the whole build (zeroing, density block maxima, the 21
- * class launches, K = A + A^T, E_K per system) is captured once as a CUDA graph and
- * replayed.  The systems' P and K pointers are read from a device table refreshed from
+ * one launch per angular class (two under HFX_MIXED: the FP64 and the FP32 share); the
+ * class launches are spread over four parallel branches (largest classes first, each to
+ * the least loaded branch) so that one class's tail overlaps the next ones; the whole
+ * build (zeroing, density block maxima, the class launches, K = A + A^T, E_K per system)
+ * is captured once as a CUDA graph and replayed.  The systems' P and K pointers are read from a device table refreshed from
  * host memory before each replay, so new buffers need no new graph.  Precision and
  * zero-block skip follow the first context's options.
  * ------------------------------------------------------------------------- */
@@ -242,6 +244,11 @@ typedef struct {
   int32_t chunk_class[21];     /* chosen quartets per dynamic claim per class */
   double tune_ms_class[21];    /* best tuning time per class, scaled from its window to the class */
   int64_t tune_window_class[21]; /* quartets in the window each candidate was timed on */
+  int32_t streams_class[21];   /* warp kernel: primitive quartets at a time per class (0: thread kernel) */
+  int32_t tune_kept;           /* 1 if the last hfx_batch_tune kept its choices (they beat the
+                                  previous ones on the whole batch), 0 if it restored them */
+  double tune_full_default_ms; /* last hfx_batch_tune: whole batch with the previous choices */
+  double tune_full_tuned_ms;   /* ... and with the tuned ones */
 } hfx_batch_stats;
 
 /* Creates a batch over n contexts (all with pair lists, same device).  Runs are ordered
@@ -250,11 +257,15 @@ typedef struct {
  * contexts must outlive the batch. */
 int hfx_batch_create(hfx_batch** out, hfx_ctx* const* ctxs, int n, void* stream);
 
-/* Autotuner: for every class, times its batched launch with each candidate group size
- * (1 or 32 lanes per quartet, where the class allows both) and dynamic chunk size on one
- * window of the class's quartets, and keeps the fastest; a candidate must beat the current
- * choice by 5% to replace it.  Uses P/K like hfx_batch_run (their K contents are
- * overwritten by the tuning launches; run hfx_batch_run afterwards).  Synchronises. */
+/* Autotuner: for every class, times its batched launch with each candidate kernel shape
+ * (a warp per quartet with 1, 2 or 4 primitive quartets at a time, or a thread per quartet
+ * where the class allows it) and dynamic chunk size (quartets per claim) on one window of
+ * the class's quartets, and keeps the fastest; a candidate must beat the current choice by
+ * 5% to replace it.  Then it times the whole batch with the previous and with the tuned
+ * choices and keeps the tuned ones only if they are faster, so tuning never makes a batch
+ * slower than its previous configuration as measured by these runs.  Uses P/K like
+ * hfx_batch_run (their K contents are overwritten; run hfx_batch_run afterwards).
+ * Synchronises. */
 int hfx_batch_tune(hfx_batch* b, const double* const* P_dev, double* const* K_dev, const int* ld);
 
 /* Builds K_s for P_s of every system s (device pointers; ld[s] >= n_bf of system s; ld

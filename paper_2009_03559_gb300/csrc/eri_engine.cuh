@@ -32,6 +32,7 @@ __device__ __constant__ float kSphCoefF[6] = {0.0f, 1.0f, -0.28867513459481287f,
 // would promote to FP64, which runs on the FP64 pipe together with the conversions)
 __device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float2 fmar(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 template <typename R>
 __device__ __forceinline__ R sph_coef(int i);
 template <>
@@ -41,21 +42,42 @@ __device__ __forceinline__ double sph_coef<double>(int i) { return kSphCoef[i]; 
 
 // Coefficients held in registers (one quartet per thread); selects avoid indexed
 // register arrays.
-struct CoefRg {
-  double PA[3], WP[3], QC[3], WQ[3];
-  double ca1, ca2, ca3, RP, ck1, ck2, ck3, RQ, cb1, cb2, cb3, cb4;
-  __device__ __forceinline__ double pa(int i) const { return i == 0 ? PA[0] : (i == 1 ? PA[1] : PA[2]); }
-  __device__ __forceinline__ double wp(int i) const { return i == 0 ? WP[0] : (i == 1 ? WP[1] : WP[2]); }
-  __device__ __forceinline__ double qc(int i) const { return i == 0 ? QC[0] : (i == 1 ? QC[1] : QC[2]); }
-  __device__ __forceinline__ double wq(int i) const { return i == 0 ? WQ[0] : (i == 1 ? WQ[1] : WQ[2]); }
-  __device__ __forceinline__ double ca(int n) const { return n == 1 ? ca1 : (n == 2 ? ca2 : ca3); }
-  __device__ __forceinline__ double ck(int n) const { return n == 1 ? ck1 : (n == 2 ? ck2 : ck3); }
-  __device__ __forceinline__ double cb(int n) const {
-    return n == 1 ? cb1 : (n == 2 ? cb2 : (n == 3 ? cb3 : cb4));
-  }
-  __device__ __forceinline__ double rp() const { return RP; }
-  __device__ __forceinline__ double rq() const { return RQ; }
+template <typename R>
+struct CoefRgT {
+  R PA[3], WP[3], QC[3], WQ[3];
+  R ca1, ca2, ca3, RP, ck1, ck2, ck3, RQ, cb1, cb2, cb3, cb4;
+  __device__ __forceinline__ R pa(int i) const { return i == 0 ? PA[0] : (i == 1 ? PA[1] : PA[2]); }
+  __device__ __forceinline__ R wp(int i) const { return i == 0 ? WP[0] : (i == 1 ? WP[1] : WP[2]); }
+  __device__ __forceinline__ R qc(int i) const { return i == 0 ? QC[0] : (i == 1 ? QC[1] : QC[2]); }
+  __device__ __forceinline__ R wq(int i) const { return i == 0 ? WQ[0] : (i == 1 ? WQ[1] : WQ[2]); }
+  __device__ __forceinline__ R ca(int n) const { return n == 1 ? ca1 : (n == 2 ? ca2 : ca3); }
+  __device__ __forceinline__ R ck(int n) const { return n == 1 ? ck1 : (n == 2 ? ck2 : ck3); }
+  __device__ __forceinline__ R cb(int n) const { return n == 1 ? cb1 : (n == 2 ? cb2 : (n == 3 ? cb3 : cb4)); }
+  __device__ __forceinline__ R rp() const { return RP; }
+  __device__ __forceinline__ R rq() const { return RQ; }
 };
+using CoefRg = CoefRgT<double>;
+
+// FP32 copy of a coefficient set (conversions on the integer units, see to_f32)
+__device__ __forceinline__ CoefRgT<float> coef_f32(const CoefRg& c, int E, int F) {
+  CoefRgT<float> f;
+  if (E > 0) {
+    for (int i = 0; i < 3; ++i) {
+      f.PA[i] = to_f32(c.PA[i]);
+      f.WP[i] = to_f32(c.WP[i]);
+    }
+    f.ca1 = to_f32(c.ca1); f.ca2 = to_f32(c.ca2); f.ca3 = to_f32(c.ca3); f.RP = to_f32(c.RP);
+  }
+  if (F > 0) {
+    for (int i = 0; i < 3; ++i) {
+      f.QC[i] = to_f32(c.QC[i]);
+      f.WQ[i] = to_f32(c.WQ[i]);
+    }
+    f.ck1 = to_f32(c.ck1); f.ck2 = to_f32(c.ck2); f.ck3 = to_f32(c.ck3); f.RQ = to_f32(c.RQ);
+    f.cb1 = to_f32(c.cb1); f.cb2 = to_f32(c.cb2); f.cb3 = to_f32(c.cb3); f.cb4 = to_f32(c.cb4);
+  }
+  return f;
+}
 
 // Scalars of one primitive quartet besides its Boys values.
 struct PrimScalars {
@@ -157,41 +179,51 @@ __device__ __forceinline__ bool prim_setup(const PrimPair& b, const PrimPair& k,
 // A coefficient set in group scratch (warp kernel) from the set-up values, in the precision
 // R of the recurrences: every set-up step runs in FP64; an FP32 set is the rounded FP64 one.
 template <typename R>
+__device__ __forceinline__ R to_R(double x) {
+  if constexpr (sizeof(R) == 4)
+    return to_f32(x);
+  else
+    return x;
+}
+
+// CS = 1: a set of R values; CS = 2 (R = float): one half of a set of float pairs (the
+// packed FP32 engine runs two primitive quartets per slot).
+template <typename R, int CS = 1>
 __device__ __forceinline__ void write_set(const PrimPair& b, const PrimPair& k, int E, int F, int Lt,
                                           const double* G, const PrimScalars& ps, R* cf) {
 #pragma unroll
   for (int m = 0; m <= kMaxLt; ++m)
-    if (m <= Lt) cf[HFX_CF_G + m] = R(G[m]);
-  cf[HFX_CF_ONE] = R(1);
-  cf[HFX_CF_ZERO] = R(0);
-  cf[HFX_CF_CA] = R(0);
-  cf[HFX_CF_CK] = R(0);
-  cf[HFX_CF_CB] = R(0);
+    if (m <= Lt) cf[(HFX_CF_G + m) * CS] = to_R<R>(G[m]);
+  cf[(HFX_CF_ONE) * CS] = to_R<R>(1);
+  cf[(HFX_CF_ZERO) * CS] = to_R<R>(0);
+  cf[(HFX_CF_CA) * CS] = to_R<R>(0);
+  cf[(HFX_CF_CK) * CS] = to_R<R>(0);
+  cf[(HFX_CF_CB) * CS] = to_R<R>(0);
   if (E > 0) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      cf[HFX_CF_PA + i] = R(b.PA[i]);
-      cf[HFX_CF_WP + i] = R(-ps.RP * ps.PQ[i]);
+      cf[(HFX_CF_PA + i) * CS] = to_R<R>(b.PA[i]);
+      cf[(HFX_CF_WP + i) * CS] = to_R<R>(-ps.RP * ps.PQ[i]);
     }
-    cf[HFX_CF_CA + 1] = R(b.inv2p);
-    cf[HFX_CF_CA + 2] = R(scale2(b.inv2p, 1));
-    cf[HFX_CF_CA + 3] = R(b.inv2p3);
-    cf[HFX_CF_RP] = R(ps.RP);
+    cf[(HFX_CF_CA + 1) * CS] = to_R<R>(b.inv2p);
+    cf[(HFX_CF_CA + 2) * CS] = to_R<R>(scale2(b.inv2p, 1));
+    cf[(HFX_CF_CA + 3) * CS] = to_R<R>(b.inv2p3);
+    cf[HFX_CF_RP * CS] = to_R<R>(-ps.RP);  // stored negated: the VRR term is V3 - rho/p V4
   }
   if (F > 0) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      cf[HFX_CF_QC + i] = R(k.PA[i]);
-      cf[HFX_CF_WQ + i] = R(ps.RQ * ps.PQ[i]);
+      cf[(HFX_CF_QC + i) * CS] = to_R<R>(k.PA[i]);
+      cf[(HFX_CF_WQ + i) * CS] = to_R<R>(ps.RQ * ps.PQ[i]);
     }
-    cf[HFX_CF_CK + 1] = R(k.inv2p);
-    cf[HFX_CF_CK + 2] = R(scale2(k.inv2p, 1));
-    cf[HFX_CF_CK + 3] = R(k.inv2p3);
-    cf[HFX_CF_RQ] = R(ps.RQ);
-    cf[HFX_CF_CB + 1] = R(scale2(ps.inv_s, -1));
-    cf[HFX_CF_CB + 2] = R(ps.inv_s);
-    cf[HFX_CF_CB + 3] = R(1.5 * ps.inv_s);
-    cf[HFX_CF_CB + 4] = R(scale2(ps.inv_s, 1));
+    cf[(HFX_CF_CK + 1) * CS] = to_R<R>(k.inv2p);
+    cf[(HFX_CF_CK + 2) * CS] = to_R<R>(scale2(k.inv2p, 1));
+    cf[(HFX_CF_CK + 3) * CS] = to_R<R>(k.inv2p3);
+    cf[HFX_CF_RQ * CS] = to_R<R>(-ps.RQ);
+    cf[(HFX_CF_CB + 1) * CS] = to_R<R>(scale2(ps.inv_s, -1));
+    cf[(HFX_CF_CB + 2) * CS] = to_R<R>(ps.inv_s);
+    cf[(HFX_CF_CB + 3) * CS] = to_R<R>(1.5 * ps.inv_s);
+    cf[(HFX_CF_CB + 4) * CS] = to_R<R>(scale2(ps.inv_s, 1));
   }
 }
 
@@ -259,7 +291,7 @@ __device__ __forceinline__ void sched_op(uint4 e, R* S, int rsz, int zero, const
   R v = fmar(cf[i1], X[e.x >> 16], X[s0]);
   v = fmar(cf[i2], X[e.y & 0xFFFF], v);
   if (w & (1u << 11))
-    v = fmar(cf[base + HFX_CF_CA + ((w >> 2) & 3)], fmar(-cf[base + HFX_CF_RP], X[e.z & 0xFFFF], X[e.y >> 16]), v);
+    v = fmar(cf[base + HFX_CF_CA + ((w >> 2) & 3)], fmar(cf[base + HFX_CF_RP], X[e.z & 0xFFFF], X[e.y >> 16]), v);
   if (w & (1u << 12)) v = fmar(cf[HFX_CF_CB + ((w >> 4) & 7)], X[e.z >> 16], v);
   X[dst] = v;
 }

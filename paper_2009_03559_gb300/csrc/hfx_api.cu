@@ -125,7 +125,7 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
       (r = ctx->alloc(&ctx->d_prim_off, n_shells)) || (r = ctx->alloc(&ctx->d_bf_off, n_shells)) ||
       (r = ctx->alloc(&ctx->d_energy, 1)) || (r = ctx->alloc(&ctx->d_busy, 1024)) ||
       (r = ctx->alloc(&ctx->d_counters, kNCnt * 21)) ||
-      (r = ctx->alloc(&ctx->d_pmax, (size_t)n_shells * n_shells)) || (r = ctx->alloc(&ctx->d_work, 32)) ||
+      (r = ctx->alloc(&ctx->d_pmax, (size_t)n_shells * n_shells)) || (r = ctx->alloc(&ctx->d_work, 64)) ||
       (r = ctx->alloc(&ctx->d_pglob, 1)))
     return bail(r);
   ctx->n_part = 2 * ctx->n_sm;
@@ -193,11 +193,11 @@ EriLaunch hfx::base_launch(hfx_ctx* ctx) {
   return L;
 }
 
-static int grid_for(hfx_ctx* ctx, int cls, int mode, long long work_items, int gs, bool mixed = false,
+static int grid_for(hfx_ctx* ctx, int cls, int mode, long long work_items, int gs, int prec = 0,
                     bool batch = false, int streams = 0) {
-  const int groups_per_block = eri_groups_per_block(mode, gs, mixed);
+  const int groups_per_block = eri_groups_per_block(gs);
   long long need = (work_items + groups_per_block - 1) / groups_per_block;
-  long long cap = (long long)eri_blocks_per_sm(cls, mode, gs, mixed, batch, streams) * ctx->n_sm;
+  long long cap = (long long)eri_blocks_per_sm(cls, mode, gs, prec, batch, streams) * ctx->n_sm;
   long long g = std::min(need, cap);
   return (int)std::max(1LL, g);
 }
@@ -287,7 +287,7 @@ extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
         L.diag_n = cnt[pc];
         L.diag_Q = ctx->d_Q;
         const int gs = eri_group_size(cls);
-        CK(eri_launch(L, cls, 1, grid_for(ctx, cls, 1, cnt[pc], gs), s, gs, false, false));
+        CK(eri_launch(L, cls, 1, grid_for(ctx, cls, 1, cnt[pc], gs), s, gs, 0, false));
       }
       start += cnt[pc];
     }
@@ -415,7 +415,7 @@ static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int pa
   L.P = P;
   L.K = K;
   L.ld = ld;
-  if (ctx->opt.schedule == HFX_SCHED_DYNAMIC) CK(cudaMemsetAsync(ctx->d_work, 0, 32 * sizeof(unsigned long long), s));
+  if (ctx->opt.schedule == HFX_SCHED_DYNAMIC) CK(cudaMemsetAsync(ctx->d_work, 0, 64 * sizeof(unsigned long long), s));
   const bool mixed = ctx->opt.precision == HFX_MIXED;
   if (ctx->opt.skip_zero_p || mixed || ctx->opt.density_tau > 0.0) {
     const bool glob = mixed && ctx->opt.fp32_pmax_global;
@@ -447,21 +447,22 @@ static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int pa
     L.q_begin = ctx->cls_qbegin[cp] + p0;
     L.q_count = p1 - p0;
     L.counters = ctx->timing ? ctx->d_counters + kNCnt * cp : nullptr;
-    // mixed precision: classes allowed FP32 run warp groups, so the FP32/FP64 choice per
-    // quartet is uniform over the lanes that work on it; the others keep the FP64 kernels
+    // mixed precision: a class allowed FP32 runs two passes over its quartet list, the
+    // quartets that stay FP64 then those whose recurrences run in FP32, each with a kernel
+    // compiled for its precision alone (registers, hence resident warps, of its own)
     L.fp32_ok = mixed && ((ctx->opt.fp32_class_mask >> cp) & 1);
-    const bool force32 = L.fp32_ok;
-    L.work = ctx->d_work + cp;
-    int gs = ctx->gs_override[cp] ? ctx->gs_override[cp] : eri_group_size(cp);
-    if (force32) gs = 32;
+    const int gs = ctx->gs_override[cp] ? ctx->gs_override[cp] : eri_group_size(cp);
     ctx->gs_used[cp] = gs;
     const int streams = ctx->streams_override[cp];
     ctx->streams_used[cp] = gs == 32 ? eri_streams(cp, streams) : 0;
     L.chunk = gs == 1 ? 256 : 8;
     const long long items = ctx->opt.schedule == HFX_SCHED_PAIR ? (L.row_end - L.row_begin) : L.q_count;
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[2 + 2 * cp], s));
-    CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items, gs, force32, false, streams), s, gs, force32, false,
-                  streams));
+    for (int pass = 0; pass < (L.fp32_ok ? 2 : 1); ++pass) {
+      const int prec = L.fp32_ok ? 1 + pass : 0;
+      L.work = ctx->d_work + cp + 21 * pass;
+      CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items, gs, prec, false, streams), s, gs, prec, false, streams));
+    }
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3 + 2 * cp], s));
     ctx->class_launched[cp] = true;
   }
@@ -548,7 +549,8 @@ extern "C" int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out) {
       st.flops_class[cp] = f64 + f32;
       fl += f64;
       fl32 += f32;
-      flr += (double)c[0] * ci.flops_prim + (double)c[1] * ci.flops_quartet;
+      st.flops_recurrence_class[cp] = (double)c[0] * ci.flops_prim + (double)c[1] * ci.flops_quartet;
+      flr += st.flops_recurrence_class[cp];
       nsp += (double)c[0] * (ctx->opt.omega > 0.0 ? 2.0 : 1.0) + (double)c[2];
     }
     st.flops_fp64 = fl;

@@ -40,6 +40,7 @@ struct BatchWork {
   bool fp32_class[21] = {};  // some system may run this class with FP32 recurrences
   long long total[21] = {};
   int gs[21] = {}, chunk[21] = {};  // lanes per quartet and dynamic chunk per class
+  int streams[21] = {};             // warp kernel: primitive quartets at a time (0 = default)
   EriLaunch *d_launch = nullptr, *h_launch = nullptr;
   BatchSys *d_sys = nullptr, *h_sys = nullptr;
   long long *d_seg = nullptr, *h_seg = nullptr;
@@ -68,7 +69,7 @@ cudaError_t bw_alloc(BatchWork& w, int cap, int n_sm) {
   if ((e = cudaMalloc(&w.d_launch, sizeof(EriLaunch) * nl)) != cudaSuccess ||
       (e = cudaMalloc(&w.d_sys, sizeof(BatchSys) * cap)) != cudaSuccess ||
       (e = cudaMalloc(&w.d_seg, sizeof(long long) * ns)) != cudaSuccess ||
-      (e = cudaMalloc(&w.d_work, sizeof(unsigned long long) * 32)) != cudaSuccess ||
+      (e = cudaMalloc(&w.d_work, sizeof(unsigned long long) * 64)) != cudaSuccess ||
       (e = cudaMalloc(&w.d_part, sizeof(double) * 2 * kBatchPart * cap)) != cudaSuccess ||
       (e = cudaMallocHost(&w.h_launch, sizeof(EriLaunch) * nl)) != cudaSuccess ||
       (e = cudaMallocHost(&w.h_sys, sizeof(BatchSys) * cap)) != cudaSuccess ||
@@ -79,11 +80,12 @@ cudaError_t bw_alloc(BatchWork& w, int cap, int n_sm) {
   return cudaSuccess;
 }
 
-// the default per-class choices: warp groups where a class needs them (or FP32 may be used)
+// the default per-class choices (those of a single-system build)
 void bw_default_choices(BatchWork& w) {
   for (int cp = 0; cp < 21; ++cp) {
-    w.gs[cp] = w.fp32_class[cp] ? 32 : eri_group_size(cp);
+    w.gs[cp] = eri_group_size(cp);
     w.chunk[cp] = w.gs[cp] == 1 ? 256 : 8;
+    w.streams[cp] = 0;
   }
 }
 
@@ -167,13 +169,15 @@ void bw_set_buffers(BatchWork& w, const double* const* P, double* const* K, cons
   }
 }
 
-EriLaunch bw_class_launch(const BatchWork& w, int cp) {
+// launch record of class cp, precision pass `pass` (0, or 0/1 for a mixed class's FP64/FP32
+// passes: each has its own work counter)
+EriLaunch bw_class_launch(const BatchWork& w, int cp, int pass = 0) {
   EriLaunch L;
   std::memset(&L, 0, sizeof(L));
   L.ci = class_info_host()[cp];
   L.schedule = HFX_SCHED_DYNAMIC;
   L.q_count = w.total[cp];
-  L.work = w.d_work + cp;
+  L.work = w.d_work + cp + 21 * pass;
   L.chunk = w.chunk[cp];
   L.n_sys = w.n;
   L.seg = w.d_seg + (size_t)cp * (w.cap + 1);
@@ -181,11 +185,12 @@ EriLaunch bw_class_launch(const BatchWork& w, int cp) {
   return L;
 }
 
-int bw_grid(const BatchWork& w, int cp, long long items) {
-  const bool mixed = w.fp32_class[cp] && w.gs[cp] > 1;
-  const long long groups_per_block = eri_groups_per_block(0, w.gs[cp], mixed);
+int bw_prec(const BatchWork& w, int cp, int pass) { return w.fp32_class[cp] ? 1 + pass : 0; }
+
+int bw_grid(const BatchWork& w, int cp, long long items, int prec) {
+  const long long groups_per_block = eri_groups_per_block(w.gs[cp]);
   const long long need = (items + groups_per_block - 1) / groups_per_block;
-  const long long cap = (long long)eri_blocks_per_sm(cp, 0, w.gs[cp], mixed, true) * w.n_sm;
+  const long long cap = (long long)eri_blocks_per_sm(cp, 0, w.gs[cp], prec, true, w.streams[cp]) * w.n_sm;
   return (int)std::max(1LL, std::min(need, cap));
 }
 
@@ -200,18 +205,61 @@ cudaError_t bw_upload(const BatchWork& w, cudaStream_t s) {
   return cudaSuccess;
 }
 
-// the whole batched build on stream s
-cudaError_t bw_enqueue(const BatchWork& w, cudaStream_t s) {
+// Parallel branches of a batched build: the class launches are spread over the main
+// stream and up to kBranches - 1 more, so that the tail of one class (its last chunks,
+// when most SMs are idle) overlaps the next classes.  Inside a graph capture the forks
+// and joins become edges of the graph.
+constexpr int kBranches = 4;
+struct Branches {
+  cudaStream_t aux[kBranches - 1] = {};
+  cudaEvent_t fork = nullptr, join[kBranches - 1] = {};
+  int n = 1;  // branches in use (1: everything on the main stream)
+};
+
+// the whole batched build on stream s (and the branches' streams, if any)
+cudaError_t bw_enqueue(const BatchWork& w, cudaStream_t s, const Branches* br = nullptr) {
   cudaError_t e;
   if ((e = bw_upload(w, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(w.d_work, 0, 32 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(w.d_work, 0, 64 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
   if ((e = launch_batch_prologue(w.d_sys, w.n, w.n_sm, w.pmax, s)) != cudaSuccess) return e;
+  const int nb = br ? br->n : 1;
+  // classes by estimated cost (quartets x FP64 flops of a quartet with 81 primitive
+  // quartets), each to the branch with the least cost so far
+  int order[21];
+  double cost[21];
   for (int cp = 0; cp < 21; ++cp) {
+    const EriClassInfo& ci = class_info_host()[cp];
+    order[cp] = cp;
+    cost[cp] = (double)w.total[cp] * (81.0 * ci.flops_prim + ci.flops_quartet);
+  }
+  std::sort(order, order + 21, [&](int a, int b) { return cost[a] > cost[b]; });
+  double load[kBranches] = {};
+  if (nb > 1) {
+    if ((e = cudaEventRecord(br->fork, s)) != cudaSuccess) return e;
+    for (int i = 0; i < nb - 1; ++i)
+      if ((e = cudaStreamWaitEvent(br->aux[i], br->fork, 0)) != cudaSuccess) return e;
+  }
+  for (int oi = 0; oi < 21; ++oi) {
+    const int cp = order[oi];
     if (w.total[cp] == 0) continue;
-    const EriLaunch L = bw_class_launch(w, cp);
-    if ((e = eri_launch(L, cp, 0, bw_grid(w, cp, w.total[cp]), s, w.gs[cp], w.fp32_class[cp] && w.gs[cp] > 1, true)) !=
-        cudaSuccess)
-      return e;
+    int bi = 0;
+    for (int i = 1; i < nb; ++i)
+      if (load[i] < load[bi]) bi = i;
+    load[bi] += cost[cp];
+    cudaStream_t bs = bi == 0 ? s : br->aux[bi - 1];
+    for (int pass = 0; pass < (w.fp32_class[cp] ? 2 : 1); ++pass) {
+      const EriLaunch L = bw_class_launch(w, cp, pass);
+      const int prec = bw_prec(w, cp, pass);
+      if ((e = eri_launch(L, cp, 0, bw_grid(w, cp, w.total[cp], prec), bs, w.gs[cp], prec, true, w.streams[cp])) !=
+          cudaSuccess)
+        return e;
+    }
+  }
+  if (nb > 1) {
+    for (int i = 0; i < nb - 1; ++i) {
+      if ((e = cudaEventRecord(br->join[i], br->aux[i])) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(s, br->join[i], 0)) != cudaSuccess) return e;
+    }
   }
   return launch_batch_epilogue(w.d_sys, w.n, w.n_sm, s);
 }
@@ -234,6 +282,9 @@ struct hfx_batch {
   bool use_graph = true;
   double tune_ms[21] = {};
   long long tune_window[21] = {};
+  double tune_full_default_ms = 0.0, tune_full_tuned_ms = 0.0;
+  int tune_kept = 0;
+  Branches br;
   float tune_target_ms = 20.f;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -268,6 +319,11 @@ extern "C" void hfx_batch_free(hfx_batch* b) {
   if (b->e1) cudaEventDestroy(b->e1);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  for (int i = 0; i < kBranches - 1; ++i) {
+    if (b->br.aux[i]) cudaStreamDestroy(b->br.aux[i]);
+    if (b->br.join[i]) cudaEventDestroy(b->br.join[i]);
+  }
+  if (b->br.fork) cudaEventDestroy(b->br.fork);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -291,11 +347,21 @@ extern "C" int hfx_batch_create(hfx_batch** out, hfx_ctx* const* ctxs, int n, vo
       (e = cudaEventCreate(&b->e1)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming)) != cudaSuccess ||
-      (e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      (e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&b->br.fork, cudaEventDisableTiming)) != cudaSuccess) {
     hfx::set_global_error(std::string("hfx_batch_create: ") + cudaGetErrorString(e));
     hfx_batch_free(b);
     return e == cudaErrorMemoryAllocation ? HFX_ERR_OOM : HFX_ERR_CUDA;
   }
+  for (int i = 0; i < kBranches - 1; ++i) {
+    if ((e = cudaStreamCreateWithFlags(&b->br.aux[i], cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->br.join[i], cudaEventDisableTiming)) != cudaSuccess) {
+      hfx::set_global_error(std::string("hfx_batch_create: ") + cudaGetErrorString(e));
+      hfx_batch_free(b);
+      return HFX_ERR_CUDA;
+    }
+  }
+  b->br.n = kBranches;
   // per-build scratch: each context's own (a context belongs to one batch build at a time)
   std::vector<double*> pmax(n), pglob(n), energy(n);
   for (int s = 0; s < n; ++s) {
@@ -341,7 +407,7 @@ extern "C" int hfx_batch_run(hfx_batch* b, const double* const* P, double* const
   if (b->use_graph) {
     if (!b->exec) {
       CKB(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      const cudaError_t r = bw_enqueue(b->w, s);
+      const cudaError_t r = bw_enqueue(b->w, s, &b->br);
       cudaGraph_t g = nullptr;
       const cudaError_t ec = cudaStreamEndCapture(s, &g);
       if (r != cudaSuccess || ec != cudaSuccess) {
@@ -353,7 +419,7 @@ extern "C" int hfx_batch_run(hfx_batch* b, const double* const* P, double* const
     }
     CKB(cudaGraphLaunch(b->exec, s));
   } else {
-    CKB(bw_enqueue(b->w, s));
+    CKB(bw_enqueue(b->w, s, &b->br));
   }
   CKB(cudaEventRecord(b->e1, s));
   CKB(cudaEventRecord(b->ev_out, s));  // later work on the caller's stream sees K and E_K
@@ -370,23 +436,51 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
   BatchWork& w = b->w;
   bw_set_buffers(w, P, K, ld);
   cudaStream_t s = b->stream;
-  CKB(bw_upload(w, s));
-  CKB(launch_batch_prologue(w.d_sys, w.n, w.n_sm, w.pmax, s));
   cudaEvent_t t0, t1;
   CKB(cudaEventCreate(&t0));
   CKB(cudaEventCreate(&t1));
-  // Each candidate runs on one window of the class's concatenated quartet list (from its
-  // middle), sized so that a launch takes about tune_target_ms: the work counter starts at
-  // the window's first index and the launch stops at its end.
+  struct Choice {
+    int gs[21], chunk[21], streams[21];
+  };
+  auto save = [&]() {
+    Choice c;
+    std::memcpy(c.gs, w.gs, sizeof(c.gs));
+    std::memcpy(c.chunk, w.chunk, sizeof(c.chunk));
+    std::memcpy(c.streams, w.streams, sizeof(c.streams));
+    return c;
+  };
+  auto restore = [&](const Choice& c) {
+    std::memcpy(w.gs, c.gs, sizeof(c.gs));
+    std::memcpy(w.chunk, c.chunk, sizeof(c.chunk));
+    std::memcpy(w.streams, c.streams, sizeof(c.streams));
+  };
+  // the whole batched build with the current choices (plain launches on the branches)
+  auto time_full = [&](double* ms_out) -> int {
+    float ms = 0.f;
+    CKB(cudaEventRecord(t0, s));
+    CKB(bw_enqueue(w, s, &b->br));
+    CKB(cudaEventRecord(t1, s));
+    CKB(cudaEventSynchronize(t1));
+    CKB(cudaEventElapsedTime(&ms, t0, t1));
+    *ms_out = ms;
+    return HFX_OK;
+  };
+  // Each candidate of a class runs on one window of the class's concatenated quartet list
+  // (from its middle), sized so that a launch takes about tune_target_ms: the work counters
+  // start at the window's first index and the launches stop at its end.
   auto time_window = [&](int cp, long long w0, long long w1, float* ms_out) -> int {
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {  // the first repetition warms caches; keep the second
-      const unsigned long long start = (unsigned long long)w0;
-      CKB(cudaMemcpyAsync(w.d_work + cp, &start, sizeof(start), cudaMemcpyHostToDevice, s));
-      EriLaunch L = bw_class_launch(w, cp);
-      L.q_count = w1;
+      const unsigned long long start[2] = {(unsigned long long)w0, (unsigned long long)w0};
+      CKB(cudaMemcpyAsync(w.d_work + cp, &start[0], sizeof(start[0]), cudaMemcpyHostToDevice, s));
+      CKB(cudaMemcpyAsync(w.d_work + cp + 21, &start[1], sizeof(start[1]), cudaMemcpyHostToDevice, s));
       CKB(cudaEventRecord(t0, s));
-      CKB(eri_launch(L, cp, 0, bw_grid(w, cp, w1 - w0), s, w.gs[cp], w.fp32_class[cp] && w.gs[cp] > 1, true));
+      for (int pass = 0; pass < (w.fp32_class[cp] ? 2 : 1); ++pass) {
+        EriLaunch L = bw_class_launch(w, cp, pass);
+        L.q_count = w1;
+        const int prec = bw_prec(w, cp, pass);
+        CKB(eri_launch(L, cp, 0, bw_grid(w, cp, w1 - w0, prec), s, w.gs[cp], prec, true, w.streams[cp]));
+      }
       CKB(cudaEventRecord(t1, s));
       CKB(cudaEventSynchronize(t1));
       CKB(cudaEventElapsedTime(&ms, t0, t1));
@@ -395,22 +489,30 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
     return HFX_OK;
   };
   int rc = HFX_OK;
+  const Choice incumbent = save();
+  double full_inc = 0.0, full_new = 0.0;
+  if ((rc = time_full(&full_inc)) != HFX_OK) return rc;
+  CKB(bw_upload(w, s));
+  CKB(launch_batch_prologue(w.d_sys, w.n, w.n_sm, w.pmax, s));
   for (int cp = 0; cp < 21 && rc == HFX_OK; ++cp) {
     const long long total = w.total[cp];
     if (total == 0) continue;
-    struct Cand { int gs, chunk; };
+    struct Cand {
+      int gs, streams, chunk;
+    };
     std::vector<Cand> cands;
-    for (int c : {4, 8, 16, 32}) cands.push_back({32, c});
-    if (!w.fp32_class[cp] && eri_group_size(cp) == 1)
-      for (int c : {128, 256, 512, 1024}) cands.push_back({1, c});
-    // window size: grow from 16k quartets until a default-candidate launch takes the target,
-    // and at least two claims for every resident warp of every candidate, so that a large
-    // chunk is not timed on a window that leaves most of the GPU idle
+    for (int k : {1, 2, 4})
+      if (eri_streams_valid(cp, k))
+        for (int c : {4, 8, 16}) cands.push_back({32, k, c});
+    if (eri_group_size(cp) == 1)
+      for (int c : {128, 256, 512}) cands.push_back({1, 0, c});
+    // window size: grow from 16k quartets until the incumbent takes the target, and at
+    // least two claims for every resident warp of every candidate, so that a large chunk
+    // is not timed on a window that leaves most of the GPU idle
     long long fill = 0;
     for (const Cand& cd : cands) {
-      const bool mx = w.fp32_class[cp] && cd.gs > 1;
-      const long long groups = (long long)eri_blocks_per_sm(cp, 0, cd.gs, mx, true) * w.n_sm *
-                               (cd.gs == 1 ? eri_block_size() / 32 : eri_groups_per_block(0, cd.gs, mx));
+      const long long groups = (long long)eri_blocks_per_sm(cp, 0, cd.gs, bw_prec(w, cp, 0), true, cd.streams) *
+                               w.n_sm * (eri_block_size() / 32);
       fill = std::max(fill, 2 * groups * cd.chunk);
     }
     long long win = std::min(total, std::max(16384LL, fill));
@@ -422,17 +524,19 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
       const double grow = ms > 0.f ? b->tune_target_ms / ms : 64.0;
       win = std::min(total, (long long)(win * std::min(64.0, std::max(2.0, grow))));
     }
+    if (rc != HFX_OK) break;
     const long long w0 = (total - win) / 2;
     // the current choice is the incumbent; a candidate must beat it by 5% to replace it
-    // (a window is one sample of the class: small gains on it did not carry to whole runs)
-    Cand bc = {w.gs[cp], w.chunk[cp]};
+    Cand bc = {w.gs[cp], w.streams[cp], w.chunk[cp]};
     float inc = 0.f;
     if ((rc = time_window(cp, w0, w0 + win, &inc)) != HFX_OK) break;
     double best = inc;
     for (const Cand& cd : cands) {
       if (rc != HFX_OK) break;
-      if (cd.gs == bc.gs && cd.chunk == bc.chunk) continue;
+      if (cd.gs == bc.gs && cd.chunk == bc.chunk && eri_streams(cp, cd.streams) == eri_streams(cp, bc.streams))
+        continue;
       w.gs[cp] = cd.gs;
+      w.streams[cp] = cd.streams;
       w.chunk[cp] = cd.chunk;
       float ms = 0.f;
       if ((rc = time_window(cp, w0, w0 + win, &ms)) != HFX_OK) break;
@@ -442,9 +546,20 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
       }
     }
     w.gs[cp] = bc.gs;
+    w.streams[cp] = bc.streams;
     w.chunk[cp] = bc.chunk;
     b->tune_ms[cp] = best * (double)total / (double)win;  // projected to the whole class
     b->tune_window[cp] = win;
+  }
+  // the tuned choices replace the incumbent only if the whole batch runs faster with them
+  if (rc == HFX_OK) rc = time_full(&full_new);
+  if (rc == HFX_OK) {
+    b->tune_full_default_ms = full_inc;
+    b->tune_full_tuned_ms = full_new;
+    b->tune_kept = full_new < full_inc;
+    if (!b->tune_kept) restore(incumbent);
+  } else {
+    restore(incumbent);
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
@@ -462,9 +577,13 @@ extern "C" int hfx_batch_get_stats(hfx_batch* b, hfx_batch_stats* out) {
     out->n_quartets += b->w.total[cp];
     out->group_size_class[cp] = b->w.gs[cp];
     out->chunk_class[cp] = b->w.chunk[cp];
+    out->streams_class[cp] = b->w.gs[cp] == 32 ? eri_streams(cp, b->w.streams[cp]) : 0;
     out->tune_ms_class[cp] = b->tune_ms[cp];
     out->tune_window_class[cp] = b->tune_window[cp];
   }
+  out->tune_full_default_ms = b->tune_full_default_ms;
+  out->tune_full_tuned_ms = b->tune_full_tuned_ms;
+  out->tune_kept = b->tune_kept;
   float ms = 0.f;
   if (b->ran && cudaEventElapsedTime(&ms, b->e0, b->e1) == cudaSuccess) out->ms_last = ms;
   return HFX_OK;

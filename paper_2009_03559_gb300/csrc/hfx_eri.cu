@@ -4,6 +4,7 @@
 // candidate pairs and stores the Schwarz factor.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 #include "eri_engine.cuh"
 #include "hfx_eri.h"
 
@@ -16,43 +17,68 @@ const EriClassInfo* class_info_host() { return kClassInfo; }
 // interleaved over the block's threads (slot k of thread t at smem[k*st + t]).
 // ---------------------------------------------------------------------------
 // ci is the launch's class record (kernel parameter space); L supplies the system's data.
-// In batched launches L lives in global memory: the fields the primitive loop needs are
-// read into registers once per quartet.
-__device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaunch& L, int bra, int ket, double* S,
+// R = float runs the recurrences and the contraction on FP32 slots, slot k in the first half
+// of the thread's own FP64 slot k (so no other lane's slots are ever touched); the
+// accumulated block is then widened in place into the FP64 slots Sd, where the horizontal
+// recurrences and the spherical step run.  R = double: the FP64 slots themselves.
+template <typename R>
+__device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaunch& L, int bra, int ket, double* Sd,
                                            int st) {
+  R* S = reinterpret_cast<R*>(Sd);
+  const int sts = st * (int)(sizeof(double) / sizeof(R));  // slot stride in units of R
   const PairArrays pa = L.pa;
   const double omega = L.omega, omega2 = L.omega2;
   const double* boys = L.boys;
-  double* V = S + ci.work_base * st;
+  R* V = S + ci.work_base * sts;
   const int nb = __ldg(pa.prim_n + bra), nk = __ldg(pa.prim_n + ket);
   const PrimPair* pb = pa.prim + __ldg(pa.prim_off + bra);
   const PrimPair* pk = pa.prim + __ldg(pa.prim_off + ket);
-  for (int a = 0; a < ci.n_acc; ++a) S[a * st] = 0.0;
+  for (int a = 0; a < ci.n_acc; ++a) S[a * sts] = R(0);
   int any = 0;
-  for (int ib = 0; ib < nb; ++ib) {
-    const PrimPair b = pb[ib];
-    for (int ik = 0; ik < nk; ++ik) {
+  // one flat loop over the primitive quartets: lanes whose quartets have the same count
+  // (the queue groups them so) run the same number of iterations
+  const int npq = nb * nk;
+  for (int t = 0; t < npq; ++t) {
+    const int ib = t / nk, ik = t - ib * nk;
+    {
+      const PrimPair b = pb[ib];
       const PrimPair k = pk[ik];
       CoefRg c;
       double Gm[kMaxLt + 1];
       if (!prim_setup(b, k, ci.E, ci.F, ci.Lt, omega, omega2, boys, c, Gm)) continue;
       ++any;
-      for (int m = 0; m <= ci.Lt; ++m) V[m * st] = Gm[m];
-      for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
-        const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = 0; o < n; ++o) vrr_bra<true>(ld_op(kVrrOps, off + o), V, S, st, c);
-      }
-      for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
-        const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-        for (int o = 0; o < n; ++o) vrr_ket<true>(ld_op(kVrrOps, off + o), V, S, st, c);
+      if constexpr (sizeof(R) == 4) {
+        const CoefRgT<float> cf = coef_f32(c, ci.E, ci.F);
+        for (int m = 0; m <= ci.Lt; ++m) V[m * sts] = to_f32(Gm[m]);
+        for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
+          const int off = ci.lv_off[lv], n = ci.lv_n[lv];
+          for (int o = 0; o < n; ++o) vrr_bra<true>(ld_op(kVrrOps, off + o), V, S, sts, cf);
+        }
+        for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
+          const int off = ci.lv_off[lv], n = ci.lv_n[lv];
+          for (int o = 0; o < n; ++o) vrr_ket<true>(ld_op(kVrrOps, off + o), V, S, sts, cf);
+        }
+      } else {
+        for (int m = 0; m <= ci.Lt; ++m) V[m * sts] = Gm[m];
+        for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
+          const int off = ci.lv_off[lv], n = ci.lv_n[lv];
+          for (int o = 0; o < n; ++o) vrr_bra<true>(ld_op(kVrrOps, off + o), V, S, sts, c);
+        }
+        for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
+          const int off = ci.lv_off[lv], n = ci.lv_n[lv];
+          for (int o = 0; o < n; ++o) vrr_ket<true>(ld_op(kVrrOps, off + o), V, S, sts, c);
+        }
       }
       for (int a = 0; a < ci.n_accl; ++a) {
         const uint32_t w = __ldg(kAccSrc + ci.acc_off + a);
-        S[(w & 0xFFFF) * st] += V[(w >> 16) * st];
+        S[(w & 0xFFFF) * sts] += V[(w >> 16) * sts];
       }
     }
   }
   if (!any) return 0;
+  if constexpr (sizeof(R) == 4) {
+    for (int a = 0; a < ci.n_acc; ++a) Sd[a * st] = to_f64(S[a * sts]);  // in place: read, then write
+  }
   double AB[3], CD[3];
   for (int i = 0; i < 3; ++i) {
     AB[i] = __ldg(pa.AB + 3 * bra + i);
@@ -60,7 +86,7 @@ __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaun
   }
   for (int s = 0; s < ci.n_post; ++s) {
     const int off = ci.post_off[s], n = ci.post_n[s], type = ci.post_type[s];
-    for (int o = 0; o < n; ++o) post_op(ld_op(kPostOps, off + o), type, S, st, AB, CD);
+    for (int o = 0; o < n; ++o) post_op(ld_op(kPostOps, off + o), type, Sd, st, AB, CD);
   }
   return any;
 }
@@ -163,7 +189,7 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedV
     // across distant pairs, run in FP64 on the group's FP64 scratch
     double* Sd = reinterpret_cast<double*>(S);
     double* tmp = reinterpret_cast<double*>(CF);
-    for (int a = lane; a < nacc; a += 32) tmp[a] = (double)S[a];
+    for (int a = lane; a < nacc; a += 32) tmp[a] = to_f64(S[a]);
     __syncwarp();
     for (int a = lane; a < nacc; a += 32) Sd[a] = tmp[a];
     __syncwarp();
@@ -174,25 +200,100 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedV
   return any;
 }
 
-// Register caps: 6 blocks of 64 threads per SM (at most 170 registers) measured fastest
-// for both kernels; the FP64 set-up phase otherwise takes registers the hot VRR loop
-// does not need and costs occupancy.
+// Packed FP32 (mixed precision): every slot and coefficient holds two primitive quartets'
+// values (a float2), so one op of the schedule advances two primitive quartets with one
+// 64-bit load per operand and one FFMA2.  The slots have the FP64 layout (8 bytes each);
+// the contracted block is widened in place to FP64 (the two halves summed in FP64) for the
+// horizontal recurrences, the spherical step and the digest.
+__device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const SchedVariant& sv, const EriLaunch& L,
+                                               int bra, int ket, double* Sd, double* CFd, int lane) {
+  float2* S = reinterpret_cast<float2*>(Sd);
+  float2* CF = reinterpret_cast<float2*>(CFd);
+  const float2 z2 = make_float2(0.f, 0.f);
+  const PairArrays pa = L.pa;
+  const double omega = L.omega, omega2 = L.omega2;
+  const double* boys = L.boys;
+  const int nb = __ldg(pa.prim_n + bra), nk = __ldg(pa.prim_n + ket);
+  const PrimPair* pb = pa.prim + __ldg(pa.prim_off + bra);
+  const PrimPair* pk = pa.prim + __ldg(pa.prim_off + ket);
+  const int k = sv.k, rsz = sv.rsz, nacc = ci.n_acc, nbase = ci.Lt + 1;
+  for (int i = lane; i < k * nacc; i += 32) {
+    const int u = i / nacc;
+    S[u * rsz + (i - u * nacc)] = z2;
+  }
+  if (lane < k) S[lane * rsz + sv.zero] = z2;
+  for (int i = lane; i < HFX_NCOEF; i += 32) CF[32 * HFX_NCOEF + i] = z2;
+  const uint4* sched = reinterpret_cast<const uint4*>(kSched) + sv.off;
+  const int npq = nb * nk;
+  int any = 0;
+  for (int base = 0; base < npq; base += 32) {
+    const int t = base + lane;
+    double G[kMaxLt + 1];
+    PrimScalars ps;
+    int ib = 0, ik = 0;
+    bool ok = false;
+    if (t < npq) {
+      ib = t / nk;
+      ik = t - ib * nk;
+      ok = prim_core(pb[ib], pk[ik], ci.Lt, omega, omega2, boys, G, ps);
+    }
+    const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    const int pos = __popc(okm & ((1u << lane) - 1u));
+    if (ok)
+      write_set<float, 2>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps,
+                          reinterpret_cast<float*>(CF + (pos >> 1) * HFX_NCOEF) + (pos & 1));
+    const int nv = __popc(okm);
+    any += nv;
+    if (nv & 1)  // the second half of the last pair: an all-zero primitive quartet
+      for (int i = lane; i < HFX_NCOEF; i += 32) reinterpret_cast<float*>(CF + (nv >> 1) * HFX_NCOEF + i)[1] = 0.f;
+    __syncwarp();
+    const int np = (nv + 1) >> 1;
+    for (int j = 0; j < np; j += k) {
+      for (int i = lane; i < k * nbase; i += 32) {
+        const int u = i / nbase, m = i - u * nbase;
+        S[u * rsz + nacc + m] = (j + u < np) ? CF[(j + u) * HFX_NCOEF + HFX_CF_G + m] : z2;
+      }
+      __syncwarp();
+      uint4 e = __ldg(sched + lane);
+      for (int it = 1; it <= sv.n_iter; ++it) {
+        const uint4 en = __ldg(sched + it * 32 + lane);
+        sched_op<float2>(e, S, rsz, sv.zero, CF, j, np);
+        __syncwarp();
+        e = en;
+      }
+    }
+  }
+  if (!any) return 0;
+  for (int a = lane; a < nacc; a += 32) {
+    float2 sum = S[a];
+    for (int u = 1; u < k; ++u) sum = __fadd2_rn(sum, S[u * rsz + a]);
+    Sd[a] = to_f64(sum.x) + to_f64(sum.y);  // in place: read, then write
+  }
+  __syncwarp();
+  post_stages<double>(ci, pa, bra, ket, Sd, lane);
+  return any;
+}
+
+// Register caps (blocks of 64 threads per SM).  Thread-per-quartet FP64: 6 (at most 170
+// registers), measured fastest; warp kernel: 8 (128 registers: the schedule keeps few values
+// live); the batched thread kernel carries the batch bookkeeping too and the FP32 passes
+// both recurrence precisions' set-up, so they get 4-6 to stay free of spills.
 #ifndef HFX_G1_MINB
 #define HFX_G1_MINB 6
 #endif
 #ifndef HFX_G32_MINB
 #define HFX_G32_MINB 8
 #endif
-// the batched thread-per-quartet kernel carries the batch bookkeeping too: 4 blocks per SM
-// keep it free of spills
 #ifndef HFX_G1B_MINB
 #define HFX_G1B_MINB 4
 #endif
-// the mixed-precision warp kernel carries both recurrence paths: 4 blocks per SM keep it
-// free of spills
-#ifndef HFX_G32M_MINB
-#define HFX_G32M_MINB 4
+#ifndef HFX_G32B_MINB
+#define HFX_G32B_MINB 8
 #endif
+
+// Precision passes of a class launch: 0 every quartet in FP64; 1 (mixed precision, first
+// pass) the quartets that must stay FP64; 2 (second pass) those whose recurrences run in FP32.
+enum { PREC_FP64 = 0, PREC_MIXED64 = 1, PREC_MIXED32 = 2 };
 
 // The digest reads P_bd, P_bc, P_ad, P_ac.  max of their max|P| (or 1 without the table):
 // 0 means the quartet contributes exactly nothing; the mixed-precision and the
@@ -203,6 +304,23 @@ __device__ __forceinline__ double pmax4(const EriLaunch& L, int sa, int sb, int 
   const size_t ns = L.ns;
   return fmax(fmax(__ldg(pm + sb * ns + sd), __ldg(pm + sb * ns + sc)),
               fmax(__ldg(pm + sa * ns + sd), __ldg(pm + sa * ns + sc)));
+}
+
+// Mixed precision: FP32 recurrences for the quartet when the class allows it and its
+// Schwarz bound times the largest density element it touches (or the largest of all of P)
+// is below fp32_tau.
+__device__ __forceinline__ bool fp32_eligible(const EriLaunch& Ls, int bra_s, int ket_s, double pm) {
+  if (!Ls.fp32_ok) return false;
+  const double pf = Ls.pglob ? __ldg(Ls.pglob) : pm;
+  return __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pf < Ls.fp32_tau;
+}
+
+// whether pass PREC takes the quartet
+template <int PREC>
+__device__ __forceinline__ bool pass_takes(const EriLaunch& Ls, int bra_s, int ket_s, double pm) {
+  if constexpr (PREC == PREC_FP64) return true;
+  const bool f32 = fp32_eligible(Ls, bra_s, ket_s, pm);
+  return PREC == PREC_MIXED32 ? f32 : !f32;
 }
 
 __device__ __forceinline__ void record_busy(const EriLaunch& L, unsigned long long t0) {
@@ -218,23 +336,29 @@ struct Tally {
   unsigned long long prim = 0, quart = 0, skip = 0, q32 = 0, p32 = 0;
 };
 
-// One quartet evaluated and digested by one lane (one quartet per thread).
+// One quartet evaluated and digested by one lane (one quartet per thread), recurrences in
+// precision R; Sd: the thread's FP64 slots.
+template <typename R>
 __device__ __forceinline__ void g1_quartet(const EriClassInfo& ci, const EriLaunch& Ls, int bra_s, int ket_s,
-                                           double* S, int st, Tally& t) {
+                                           double* Sd, int st, Tally& t) {
   const int bra = __ldg(Ls.sorted + bra_s), ket = __ldg(Ls.sorted + ket_s);
   const int sa = __ldg(Ls.pa.sa + bra), sb = __ldg(Ls.pa.sb + bra);
   const int sc = __ldg(Ls.pa.sa + ket), sd = __ldg(Ls.pa.sb + ket);
   const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
-  const int ne = contract_g1(ci, Ls, bra, ket, S, st);
+  const int ne = contract_g1<R>(ci, Ls, bra, ket, Sd, st);
   t.prim += ne;
   t.skip += npq - ne;
   if (!ne) return;
   ++t.quart;
+  if (sizeof(R) == 4) {
+    ++t.q32;
+    t.p32 += ne;
+  }
   double deg = 1.0;
   if (sa == sb) deg *= 0.5;
   if (sc == sd) deg *= 0.5;
   if (bra_s == ket_s) deg *= 0.5;
-  digest(ci, S + ci.out_base * st, st, __ldg(Ls.sh.bf_off + sa), __ldg(Ls.sh.bf_off + sb), __ldg(Ls.sh.bf_off + sc),
+  digest(ci, Sd + ci.out_base * st, st, __ldg(Ls.sh.bf_off + sa), __ldg(Ls.sh.bf_off + sb), __ldg(Ls.sh.bf_off + sc),
          __ldg(Ls.sh.bf_off + sd), deg, Ls.P, Ls.K, Ls.ld, 0, 1);
 }
 
@@ -272,9 +396,9 @@ __device__ __forceinline__ void sort64_desc(int& k0, int& k1, int lane) {
   }
 }
 
-template <bool BATCH>
-__device__ __forceinline__ void g1_drain(const EriLaunch& L, const EriClassInfo& ci, G1Queue& Q, int lane, double* S,
-                                         int st, Tally& t, bool all) {
+template <bool BATCH, typename R>
+__device__ __forceinline__ void g1_drain(const EriLaunch& L, const EriClassInfo& ci, G1Queue& Q, int lane,
+                                         double* Sd, int st, Tally& t, bool all) {
   while (Q.n >= 32 || (all && Q.n > 0)) {
     int4 e;
     int take;
@@ -295,15 +419,15 @@ __device__ __forceinline__ void g1_drain(const EriLaunch& L, const EriClassInfo&
     }
     __syncwarp();
     Q.n -= take;
-    if (lane < take) g1_quartet(ci, BATCH ? L.batch[e.x] : L, e.y, e.z, S, st, t);
+    if (lane < take) g1_quartet<R>(ci, BATCH ? L.batch[e.x] : L, e.y, e.z, Sd, st, t);
   }
 }
 
 // Quartets [q0, q1) of the launch record Ls (system sys), one quartet per thread: the warp
 // tests 32 consecutive quartets at a time and queues the survivors.
-template <bool BATCH>
+template <bool BATCH, int PREC, typename R>
 __device__ __forceinline__ void g1_range(const EriLaunch& L, const EriClassInfo& ci, const EriLaunch& Ls, int sys,
-                                         long long q0, long long q1, double* S, int st, int lane, G1Queue& Q,
+                                         long long q0, long long q1, double* Sd, int st, int lane, G1Queue& Q,
                                          Tally& t) {
   const long long* qoff = Ls.qoff;
   const int row_begin = Ls.row_begin, bra0 = Ls.bra_bin_start, ket0 = Ls.ket_bin_start;
@@ -322,24 +446,23 @@ __device__ __forceinline__ void g1_range(const EriLaunch& L, const EriClassInfo&
       const int bra = __ldg(Ls.sorted + bra_s), ket = __ldg(Ls.sorted + ket_s);
       const double pm = pmax4(Ls, __ldg(Ls.pa.sa + bra), __ldg(Ls.pa.sb + bra), __ldg(Ls.pa.sa + ket),
                               __ldg(Ls.pa.sb + ket));
-      keep = !(skip && pm == 0.0) && !(dens > 0.0 && __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pm < dens);
+      keep = !(skip && pm == 0.0) && !(dens > 0.0 && __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pm < dens) &&
+             pass_takes<PREC>(Ls, bra_s, ket_s, pm);
       npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
     }
     const unsigned m = __ballot_sync(0xffffffffu, keep);
     if (keep) Q.q[Q.n + __popc(m & ((1u << lane) - 1u))] = make_int4(sys, bra_s, ket_s, npq);
     Q.n += __popc(m);
     __syncwarp();
-    g1_drain<BATCH>(L, ci, Q, lane, S, st, t, false);
+    g1_drain<BATCH, R>(L, ci, Q, lane, Sd, st, t, false);
   }
 }
 
 // Quartets [q0, q1) of the launch record Ls, one warp: the warp takes them one by one.
 // ci and sv: the launch's class record and schedule variant.
-template <bool MIXED>
+template <int PREC>
 __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const SchedVariant& sv, const EriLaunch& Ls,
                                           long long q0, long long q1, double* S, double* CF, int lane, Tally& t) {
-  float* Sf = reinterpret_cast<float*>(S);  // the FP32 engine reuses the group's memory
-  float* CFf = reinterpret_cast<float*>(CF);
   if (q0 >= q1) return;
   int r = find_row(Ls.qoff, Ls.row_begin, Ls.row_end, q0);
   for (long long q = q0; q < q1; ++q) {
@@ -353,18 +476,13 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const SchedVar
     if (Ls.skip_zero && pm == 0.0) continue;
     // density-weighted screening (off when dens_tau = 0)
     if (Ls.dens_tau > 0.0 && __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pm < Ls.dens_tau) continue;
-    // mixed precision: FP32 recurrences when the Schwarz bound times the largest density
-    // element the quartet touches (or the largest of all of P) is below fp32_tau
-    // (warp-uniform decision)
-    bool f32 = false;
-    if (MIXED && Ls.fp32_ok) {
-      const double pf = Ls.pglob ? __ldg(Ls.pglob) : pm;
-      f32 = __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pf < Ls.fp32_tau;
-    }
+    // mixed precision: this pass's share of the quartets (warp-uniform decision)
+    if (!pass_takes<PREC>(Ls, bra_s, ket_s, pm)) continue;
     const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
+    const bool f32 = PREC == PREC_MIXED32;
     int ne;
-    if (MIXED && f32)
-      ne = contract_g32<float>(ci, sv, Ls, bra, ket, Sf, CFf, lane);
+    if (f32)
+      ne = contract_g32_x2(ci, sv, Ls, bra, ket, S, CF, lane);
     else
       ne = contract_g32<double>(ci, sv, Ls, bra, ket, S, CF, lane);
     t.prim += ne;
@@ -435,38 +553,40 @@ __device__ __forceinline__ void flush_tally(const EriLaunch& L, const Tally& t) 
   atomicAdd(L.counters + 4, t.p32);
 }
 
-template <int MODE, bool BATCH>
-__global__ void __launch_bounds__(64, BATCH ? HFX_G1B_MINB : HFX_G1_MINB) eri_g1_kernel(const EriLaunch L) {
+template <int MODE, int PREC, bool BATCH>
+__global__ void __launch_bounds__(64, (BATCH || PREC == PREC_MIXED32) ? HFX_G1B_MINB : HFX_G1_MINB)
+    eri_g1_kernel(const EriLaunch L) {
   extern __shared__ double smem[];
   const int st = blockDim.x;
-  double* S = smem + threadIdx.x;
+  double* Sd = smem + threadIdx.x;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long ng = (long long)gridDim.x * blockDim.x;
   unsigned long long t0 = 0;
   if (L.busy && threadIdx.x == 0) t0 = globaltimer_ns();
   if (MODE == 0) {
+    using R = typename std::conditional<PREC == PREC_MIXED32, float, double>::type;
     const int lane = threadIdx.x & 31;
     Tally t;
     G1Queue Q{reinterpret_cast<int4*>(smem + (size_t)L.ci.scratch * blockDim.x) + (threadIdx.x >> 5) * 64, 0};
     for_each_range<BATCH, 32>(L, gid >> 5, ng >> 5, lane, 0xffffffffu,
                               [&](const EriLaunch& Ls, int sys, long long q0, long long q1) {
-                                g1_range<BATCH>(L, L.ci, Ls, sys, q0, q1, S, st, lane, Q, t);
+                                g1_range<BATCH, PREC, R>(L, L.ci, Ls, sys, q0, q1, Sd, st, lane, Q, t);
                               });
-    g1_drain<BATCH>(L, L.ci, Q, lane, S, st, t, true);
+    g1_drain<BATCH, R>(L, L.ci, Q, lane, Sd, st, t, true);
     flush_tally(L, t);
   } else {
     for (long long t = gid; t < L.diag_n; t += ng) {
       const int p = __ldg(L.diag_list + t);
       double mx = 0.0;
-      if (contract_g1(L.ci, L, p, p, S, st)) mx = diag_max(L.ci, S + L.ci.out_base * st, st);
+      if (contract_g1<double>(L.ci, L, p, p, Sd, st)) mx = diag_max(L.ci, Sd + L.ci.out_base * st, st);
       L.diag_Q[p] = sqrt(mx);
     }
   }
   record_busy(L, t0);
 }
 
-template <int MODE, bool MIXED, bool BATCH>
-__global__ void __launch_bounds__(64, MIXED ? HFX_G32M_MINB : HFX_G32_MINB) eri_g32_kernel(const EriLaunch L) {
+template <int MODE, int PREC, bool BATCH>
+__global__ void __launch_bounds__(64, BATCH ? HFX_G32B_MINB : HFX_G32_MINB) eri_g32_kernel(const EriLaunch L) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int gpb = blockDim.x >> 5;
@@ -480,7 +600,7 @@ __global__ void __launch_bounds__(64, MIXED ? HFX_G32M_MINB : HFX_G32_MINB) eri_
     Tally t;
     for_each_range<BATCH, 32>(L, gid, ng, lane, 0xffffffffu,
                               [&](const EriLaunch& Ls, int, long long q0, long long q1) {
-                                g32_range<MIXED>(L.ci, L.sv, Ls, q0, q1, S, CF, lane, t);
+                                g32_range<PREC>(L.ci, L.sv, Ls, q0, q1, S, CF, lane, t);
                               });
     if (lane == 0) flush_tally(L, t);
   } else {
@@ -545,22 +665,21 @@ int eri_streams(int cls, int streams) {
 }
 
 // The kernel instance for a class launch.  gs: lanes per quartet (1 = a thread, 32 = a warp);
-// mode 1 = Schwarz diagonal; batch = quartets of several systems in one launch.
-static const void* kernel_ptr(int mode, int gs, bool mixed, bool batch) {
-  if (gs == 1) {
-    if (mode == 1) return (const void*)eri_g1_kernel<1, false>;
-    return batch ? (const void*)eri_g1_kernel<0, true> : (const void*)eri_g1_kernel<0, false>;
-  }
-  if (mode == 1) return (const void*)eri_g32_kernel<1, false, false>;
-  if (mixed) return batch ? (const void*)eri_g32_kernel<0, true, true> : (const void*)eri_g32_kernel<0, true, false>;
-  return batch ? (const void*)eri_g32_kernel<0, false, true> : (const void*)eri_g32_kernel<0, false, false>;
+// mode 1 = Schwarz diagonal; prec: precision pass; batch = quartets of several systems.
+template <int PREC>
+static const void* kernel_ptr_p(int gs, bool batch) {
+  if (gs == 1) return batch ? (const void*)eri_g1_kernel<0, PREC, true> : (const void*)eri_g1_kernel<0, PREC, false>;
+  return batch ? (const void*)eri_g32_kernel<0, PREC, true> : (const void*)eri_g32_kernel<0, PREC, false>;
 }
 
-// the group size a launch actually runs with
-static int effective_gs(int mode, int gs, bool mixed) {
-  if (gs == 1) return 1;
-  return 32;
+static const void* kernel_ptr(int mode, int gs, int prec, bool batch) {
+  if (mode == 1) return gs == 1 ? (const void*)eri_g1_kernel<1, 0, false> : (const void*)eri_g32_kernel<1, 0, false>;
+  if (prec == PREC_MIXED64) return kernel_ptr_p<PREC_MIXED64>(gs, batch);
+  if (prec == PREC_MIXED32) return kernel_ptr_p<PREC_MIXED32>(gs, batch);
+  return kernel_ptr_p<PREC_FP64>(gs, batch);
 }
+
+static int effective_gs(int gs) { return gs == 1 ? 1 : 32; }
 
 size_t eri_smem_bytes(int cls, int gs, int streams) {
   // one quartet per thread: interleaved scratch, then a 64-entry quartet queue per warp
@@ -581,34 +700,36 @@ cudaError_t eri_prepare() {
       if (kSchedInfo[c][i].k) mx = std::max(mx, eri_smem_bytes(c, 32, kSchedInfo[c][i].k));
   }
   if (mx > 227 * 1024) mx = 227 * 1024;
-  for (int mode = 0; mode < 2; ++mode)
-    for (int gs : {1, 32})
-      for (int mixed = 0; mixed < 2; ++mixed)
-        for (int batch = 0; batch < 2; ++batch) {
-          cudaError_t e = cudaFuncSetAttribute(kernel_ptr(mode, gs, mixed, batch),
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-          if (e != cudaSuccess) return e;
-        }
+  for (int gs : {1, 32}) {
+    cudaError_t e = cudaFuncSetAttribute(kernel_ptr(1, gs, 0, false), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)mx);
+    if (e != cudaSuccess) return e;
+    for (int prec = 0; prec < 3; ++prec)
+      for (int batch = 0; batch < 2; ++batch) {
+        e = cudaFuncSetAttribute(kernel_ptr(0, gs, prec, batch), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+        if (e != cudaSuccess) return e;
+      }
+  }
   return cudaSuccess;
 }
 
-int eri_blocks_per_sm(int cls, int mode, int gs, bool mixed, bool batch, int streams) {
+int eri_blocks_per_sm(int cls, int mode, int gs, int prec, bool batch, int streams) {
   int n = 0;
-  const int g = effective_gs(mode, gs, mixed);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(mode, g, mixed, batch), kBlock,
+  const int g = effective_gs(gs);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(mode, g, prec, batch), kBlock,
                                                     eri_smem_bytes(cls, g, streams)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
 
-int eri_groups_per_block(int mode, int gs, bool mixed) { return kBlock / effective_gs(mode, gs, mixed); }
+int eri_groups_per_block(int gs) { return kBlock / effective_gs(gs); }
 
-cudaError_t eri_launch(const EriLaunch& L0, int cls, int mode, int grid, cudaStream_t stream, int gs, bool mixed,
+cudaError_t eri_launch(const EriLaunch& L0, int cls, int mode, int grid, cudaStream_t stream, int gs, int prec,
                        bool batch, int streams) {
-  const int g = effective_gs(mode, gs, mixed);
+  const int g = effective_gs(gs);
   const size_t smem = eri_smem_bytes(cls, g, streams);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  const void* k = kernel_ptr(mode, g, mixed, batch);
+  const void* k = kernel_ptr(mode, g, prec, batch);
   EriLaunch L = L0;
   if (g == 32) L.sv = kSchedInfo[cls][variant_index(cls, streams)];
   void* args[] = {(void*)&L};

@@ -100,6 +100,23 @@ __device__ __forceinline__ double scale2(double x, int e) {
 // x >= 2^e... comparisons of non-negative doubles on the high word (integer units).
 __device__ __forceinline__ bool ge_hi(double x, int hi) { return __double2hiint(x) >= hi; }
 
+// FP32 value of any finite double by truncation of the mantissa (relative error below
+// 2^-23): magnitudes below 2^-126 give 0, above 2^128 are not expected.
+__device__ __forceinline__ float to_f32(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int mag = hi & 0x7fffffff;
+  const unsigned fb = ((unsigned)(mag - (896 << 20)) << 3) | (lo >> 29);
+  return __int_as_float((int)((mag < (897 << 20) ? 0u : fb) | ((unsigned)hi & 0x80000000u)));
+}
+// Exact double of a float (subnormal floats give 0).
+__device__ __forceinline__ double to_f64(float f) {
+  const int fb = __float_as_int(f);
+  const int mag = fb & 0x7fffffff;
+  if (mag < 0x00800000) return 0.0;
+  return __hiloint2double(((mag >> 3) + (896 << 20)) | (fb & (int)0x80000000), mag << 29);
+}
+
 // 1/sqrt(x) for x > 0 in FP32 range: FP32 hardware seed (relative error below 2^-22),
 // one Newton-Raphson step (the error squares: below 1e-13 relative).  3 FP64 instructions.
 __device__ __forceinline__ double rsqrt_nr(double x) {

@@ -28,7 +28,7 @@ CLASS_SPH_SIZE = [_PAIR_SIZE[hi] * _PAIR_SIZE[lo] for hi in range(6) for lo in r
 # quartet classes without d shells (bra and ket pair classes among ss, ps, pp)
 SP_CLASS_MASK = sum(1 << (hi * (hi + 1) // 2 + lo) for hi in range(3) for lo in range(hi + 1))
 ALL_CLASS_MASK = (1 << 21) - 1
-FP32_CLASSES_DEFAULT = 0xFFB30  # HFX_FP32_CLASSES_DEFAULT in include/hfx.h
+FP32_CLASSES_DEFAULT = 0xFFFFF  # HFX_FP32_CLASSES_DEFAULT in include/hfx.h
 
 
 class Options(ctypes.Structure):
@@ -76,7 +76,8 @@ class Stats(ctypes.Structure):
                 ("ms_pairs", ctypes.c_double), ("ms_build", ctypes.c_double),
                 ("ms_class", ctypes.c_double * 21), ("energy", ctypes.c_double),
                 ("flops_recurrence", ctypes.c_double), ("special_evals", ctypes.c_double),
-                ("streams_class", ctypes.c_int32 * 21), ("reserved_stats", ctypes.c_int32 * 1)]
+                ("streams_class", ctypes.c_int32 * 21), ("reserved_stats", ctypes.c_int32 * 1),
+                ("flops_recurrence_class", ctypes.c_double * 21)]
 
     def as_dict(self):
         return {
@@ -92,20 +93,26 @@ class Stats(ctypes.Structure):
             "energy": float(self.energy),
             "flops_recurrence": float(self.flops_recurrence), "special_evals": float(self.special_evals),
             "streams_class": [int(x) for x in self.streams_class],
+            "flops_recurrence_class": [float(x) for x in self.flops_recurrence_class],
         }
 
 
 class BatchStats(ctypes.Structure):
     _fields_ = [("n_quartets", ctypes.c_int64), ("ms_last", ctypes.c_double),
                 ("group_size_class", ctypes.c_int32 * 21), ("chunk_class", ctypes.c_int32 * 21),
-                ("tune_ms_class", ctypes.c_double * 21), ("tune_window_class", ctypes.c_int64 * 21)]
+                ("tune_ms_class", ctypes.c_double * 21), ("tune_window_class", ctypes.c_int64 * 21),
+                ("streams_class", ctypes.c_int32 * 21), ("tune_kept", ctypes.c_int32),
+                ("tune_full_default_ms", ctypes.c_double), ("tune_full_tuned_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {"n_quartets": int(self.n_quartets), "ms_last": float(self.ms_last),
                 "group_size_class": [int(x) for x in self.group_size_class],
                 "chunk_class": [int(x) for x in self.chunk_class],
                 "tune_ms_class": [float(x) for x in self.tune_ms_class],
-                "tune_window_class": [int(x) for x in self.tune_window_class]}
+                "tune_window_class": [int(x) for x in self.tune_window_class],
+                "streams_class": [int(x) for x in self.streams_class], "tune_kept": int(self.tune_kept),
+                "tune_full_default_ms": float(self.tune_full_default_ms),
+                "tune_full_tuned_ms": float(self.tune_full_tuned_ms)}
 
 
 _lib = None
