@@ -95,6 +95,14 @@ typedef struct {
                           density_tau; it changes K by at most that bound per dropped quartet
                           and block element, and extends the exact-zero skip to small
                           densities (Sec. 3.1 screening with the density folded in) */
+  double dist_tau;     /* distance-aware screening (default 0 = off): a quartet is also dropped
+                          when Q_IJ Q_KL exp(-kappa rho R^2) < dist_tau, the short-range
+                          kernel's decay between the two pair distributions (rho from the pairs'
+                          smallest exponent sums p, q: pq/(p+q); kappa = omega^2/(omega^2+rho);
+                          R the distance of their most diffuse primitive-pair centres less the
+                          spread of each pair's primitive-pair centres).  For s-type primitive
+                          quartets the factor bounds the integral; for higher angular momentum
+                          it is an estimate (measured far below the true factor) */
 } hfx_options;
 
 typedef struct {
@@ -126,6 +134,46 @@ typedef struct {
   int32_t reserved_stats[1];
   double flops_recurrence_class[21]; /* flops_recurrence per class */
 } hfx_stats;
+
+/* ---------------------------------------------------------------------------
+ * Periodic images: the lattice sums of Eq. vx (Sec. 2) for a crystal.
+ *
+ *   K^G_{mu lambda} = sum_{N,H} sum_{nu sigma} (mu^0 nu^N | lambda^G sigma^H) P^{H-N}_{nu sigma}
+ *
+ * mu, lambda run over the home cell's functions, nu^N over those of cell N, sigma^H of
+ * cell H; P^R couples a home-cell function to one of cell R.  The library builds list-IJ
+ * in the home cell (every pair with one shell in the home cell and its partner in any cell
+ * within the orbital cutoff 2 r_c, Sec. 3.1), Schwarz-screens it like the molecular list
+ * (Q_max over the crystal), and for each requested cell G evaluates every quartet (p | q + G)
+ * of two such pairs with Q_p Q_q >= tau whose density block exists (list-KL over the
+ * supercell, Sec. 3.1), in FP64 by the same kernels with the ket pair translated by G.  A
+ * quartet whose density cell offset is not in the given list contributes nothing.
+ * ------------------------------------------------------------------------- */
+
+/* Creates a periodic context: the home cell (n_atoms atoms at xyz, shells as in
+ * hfx_init_basis) and lattice[9] (rows: the three cell vectors, bohr; host).  The options
+ * must set rcut_bohr > 0 (the cutoff bounds the image sums) and precision HFX_FP64.  The
+ * library replicates the cell over the box of cells the cutoff can reach (at most 8 in
+ * each direction) and keeps that image basis on the device.  Errors: HFX_ERR_ARG (no
+ * cutoff, degenerate lattice, cutoff reaching too far), the hfx_init_basis errors. */
+int hfx_init_periodic(hfx_ctx** out, int n_atoms, const double* xyz, const double* lattice, int n_shells,
+                      const int* shell_atom, const int* shell_l, const int* shell_nprim, const double* alpha,
+                      const double* coef, const hfx_options* opt, void* stream);
+
+/* Integer cell coordinates of the image box (3 per cell, home cell first) into cells[3*max_n]
+ * (host, may be NULL); returns the number of cells, or HFX_ERR_ARG for a molecular context. */
+int hfx_periodic_cells(const hfx_ctx* ctx, int* cells, int max_n);
+
+/* K^G for n_G cells.  R_cells[3*n_R] (host): the cell offsets R of the density blocks;
+ * P_R (device): n_R blocks P^R, each n_bf x n_bf row-major (n_bf of the home cell), in the
+ * order of R_cells.  G_cells[3*n_G] (host); K_G (device): n_G blocks K^G written in full
+ * (zeroed first).  For a cell whose opposite -G comes earlier in G_cells, K^G is the
+ * transpose of K^{-G} (exchanging bra and ket pairs maps one lattice sum onto the other;
+ * the density blocks must satisfy P^{-R} = (P^R)^T, as a real density does).  Asynchronous
+ * on the context's stream.  Errors: HFX_ERR_STATE (not a
+ * periodic context, no pair list), HFX_ERR_ARG (empty lists, a repeated R, |R_i| > 32). */
+int hfx_build_K_periodic(hfx_ctx* ctx, int n_R, const int* R_cells, const double* P_R, int n_G, const int* G_cells,
+                         double* K_G);
 
 /* Primitive quartets the warp kernel runs at a time for quartet class cls (0..20) in later
  * builds: 0 = the class default, else one of the variants the library carries (1, 2 or 4;

@@ -93,6 +93,12 @@ def lib():
             L.ora_build_K.restype = ctypes.c_double
             L.ora_build_K_dens.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
             L.ora_build_K_dens.restype = ctypes.c_double
+            L.ora_build_K_dist.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
+            L.ora_build_K_dist.restype = ctypes.c_double
+            L.ora_dist_estimate.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.ora_dist_estimate.restype = ctypes.c_double
+            L.ora_screen_export_dist.argtypes = [vp, dp, dp]
+            L.ora_screen_export_dist.restype = None
             L.ora_K_block.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int, dp]
             L.ora_K_block.restype = ctypes.c_int
             L.ora_trace_PK.argtypes = [ctypes.c_int, dp, dp]
@@ -237,6 +243,27 @@ class Screen:
         ek = lib().ora_build_K_dens(self.h, _dp(P), 0 if mode == "plain" else 1, int(nthreads),
                                     float(dens_tau), _dp(K), _dp(pm))
         return K, float(ek), pm.reshape(ns, ns)
+
+    def build_K_dist(self, P: np.ndarray, dist_tau: float, mode: str = "sym", nthreads: int = 0):
+        """K with the distance-aware quartet test (hfx_oracle.c, ora_build_K_dist)."""
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        nb = self.basis.n_bf
+        K = np.zeros((nb, nb))
+        e = lib().ora_build_K_dist(self.h, _dp(P), 0 if mode == "plain" else 1, nthreads, float(dist_tau), _dp(K))
+        return K, e
+
+    def dist_estimate(self, I: int, J: int, K: int, L: int) -> float:
+        """Q_IJ Q_KL exp(-kappa rho R^2) of the distance-aware test."""
+        return lib().ora_dist_estimate(self.h, int(I), int(J), int(K), int(L))
+
+    def export_dist(self):
+        """Pair data of the distance-aware test: (n, n, 4) centre xyz and spread, (n, n) the
+        smallest exponent sum."""
+        ns = self.basis.n_shells
+        pst = np.zeros(ns * ns * 4)
+        pexp = np.zeros(ns * ns)
+        lib().ora_screen_export_dist(self.h, _dp(pst), _dp(pexp))
+        return pst.reshape(ns, ns, 4), pexp.reshape(ns, ns)
 
     def K_block(self, P: np.ndarray, I: int, Ks: int) -> np.ndarray:
         P = np.ascontiguousarray(P, dtype=np.float64)

@@ -538,6 +538,12 @@ typedef struct {
    * (n_shells^2) and the threshold; NULL / 0 otherwise */
   const double *pm;
   double dens_tau;
+  /* distance-aware screening (ora_build_K_dist): threshold, and per shell pair (n_shells^2,
+   * symmetric) the centre of its most diffuse primitive pair (3), the largest distance of
+   * any of its primitive-pair centres from that point, and the smallest exponent sum */
+  double dist_tau;
+  double *pst;   /* 4 per pair: centre xyz, spread */
+  double *pexp;  /* smallest exponent sum */
   double *Q;        /* n_shells^2, symmetric: sqrt(max |(mu nu|mu nu)|) */
   unsigned char *cut_ok; /* n_shells^2: orbital-cutoff test passed */
   unsigned char *kept;   /* n_shells^2: pair kept for the quartet loops */
@@ -560,7 +566,7 @@ static int cutoff_ok(const ora_basis *B, int I, int J, double rcut) {
 void ora_screen_free(void *vs) {
   ora_screen *s = (ora_screen *)vs;
   if (!s) return;
-  free(s->Q); free(s->cut_ok); free(s->kept);
+  free(s->Q); free(s->cut_ok); free(s->kept); free(s->pst); free(s->pexp);
   free(s);
 }
 
@@ -610,7 +616,67 @@ void *ora_screen_new(const void *vb, double omega, double tau, double rcut, int 
     if (s->cut_ok[i] && s->Q[i] > qm) qm = s->Q[i];
   s->Qmax = qm;
   for (size_t i = 0; i < nn; ++i) s->kept[i] = (unsigned char)(s->cut_ok[i] && s->Q[i] * qm >= tau);
+  /* pair data of the distance-aware test: a, b the smallest exponents of the two shells,
+   * P* = (a A + b B)/(a + b); every primitive-pair centre (x A + y B)/(x + y) lies on AB,
+   * at |x/(x+y) - a/(a+b)| |AB| from P* */
+  s->pst = (double *)calloc(4 * (nn > 0 ? nn : 1), sizeof(double));
+  s->pexp = (double *)calloc(nn > 0 ? nn : 1, sizeof(double));
+  for (int I = 0; I < n; ++I)
+    for (int J = 0; J < n; ++J) {
+      const double *A = B->xyz + 3 * B->atom[I], *Bc = B->xyz + 3 * B->atom[J];
+      double a = B->alpha[B->prim_off[I]], b = B->alpha[B->prim_off[J]];
+      for (int k = 1; k < B->nprim[I]; ++k)
+        if (B->alpha[B->prim_off[I] + k] < a) a = B->alpha[B->prim_off[I] + k];
+      for (int k = 1; k < B->nprim[J]; ++k)
+        if (B->alpha[B->prim_off[J] + k] < b) b = B->alpha[B->prim_off[J] + k];
+      double ab = 0.0;
+      for (int i = 0; i < 3; ++i) {
+        s->pst[4 * ((size_t)I * n + J) + i] = (a * A[i] + b * Bc[i]) / (a + b);
+        ab += (A[i] - Bc[i]) * (A[i] - Bc[i]);
+      }
+      ab = sqrt(ab);
+      double sp = 0.0;
+      for (int k = 0; k < B->nprim[I]; ++k)
+        for (int kk = 0; kk < B->nprim[J]; ++kk) {
+          double x = B->alpha[B->prim_off[I] + k], y = B->alpha[B->prim_off[J] + kk];
+          double d = fabs(x / (x + y) - a / (a + b)) * ab;
+          if (d > sp) sp = d;
+        }
+      s->pst[4 * ((size_t)I * n + J) + 3] = sp;
+      s->pexp[(size_t)I * n + J] = a + b;
+    }
   return s;
+}
+
+/* the distance-aware pair data (n_shells^2 x 4 and n_shells^2) */
+void ora_screen_export_dist(const void *vs, double *pst, double *pexp) {
+  const ora_screen *s = (const ora_screen *)vs;
+  size_t nn = (size_t)s->B->n_shells * s->B->n_shells;
+  if (pst) memcpy(pst, s->pst, 4 * nn * sizeof(double));
+  if (pexp) memcpy(pexp, s->pexp, nn * sizeof(double));
+}
+
+/* Distance-aware estimate of the largest |(mu nu|lambda sigma)| of the shell quartet (IJ|KL):
+ * Q_IJ Q_KL exp(-kappa rho R^2) with rho = p q / (p + q) from the two pairs' smallest exponent
+ * sums p, q, kappa = omega^2 / (omega^2 + rho), and R the distance between their most
+ * diffuse primitive-pair centres less both spreads (0 if negative).  For s-type primitive
+ * quartets it bounds every primitive term (G_0(T) <= G_0(0) exp(-kappa T), T >= rho R^2 for
+ * the slowest-decaying pair); for higher angular momentum it is an estimate. */
+double ora_dist_estimate(const void *vs, int I, int J, int K, int L) {
+  const ora_screen *s = (const ora_screen *)vs;
+  int n = s->B->n_shells;
+  size_t ij = (size_t)I * n + J, kl = (size_t)K * n + L;
+  double r2 = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    double t = s->pst[4 * ij + i] - s->pst[4 * kl + i];
+    r2 += t * t;
+  }
+  double r = sqrt(r2) - s->pst[4 * ij + 3] - s->pst[4 * kl + 3];
+  if (r < 0.0) r = 0.0;
+  double p = s->pexp[ij], q = s->pexp[kl];
+  double rho = p * q / (p + q), om2 = s->omega * s->omega;
+  double lam = om2 * rho / (om2 + rho);
+  return s->Q[ij] * s->Q[kl] * exp(-lam * r * r);
 }
 
 void ora_screen_export(const void *vs, double *Q, unsigned char *cut_ok, unsigned char *kept,
@@ -622,6 +688,8 @@ void ora_screen_export(const void *vs, double *Q, unsigned char *cut_ok, unsigne
   if (kept) memcpy(kept, s->kept, nn);
   if (qmax) *qmax = s->Qmax;
 }
+
+double ora_dist_estimate(const void *vs, int I, int J, int K, int L);
 
 static inline int keep4(const ora_screen *s, int I, int J, int K, int L) {
   int n = s->B->n_shells;
@@ -640,6 +708,7 @@ static inline int keep4(const ora_screen *s, int I, int J, int K, int L) {
     if (t > m) m = t;
     if (s->Q[ij] * s->Q[kl] * m < s->dens_tau) return 0;
   }
+  if (s->dist_tau > 0.0 && ora_dist_estimate(s, I, J, K, L) < s->dist_tau) return 0;
   return 1;
 }
 
@@ -841,6 +910,17 @@ double ora_build_K_dens(void *vs, const double *P, int mode, int nthreads, doubl
   s->pm = NULL;
   s->dens_tau = 0.0;
   free(pm);
+  return e;
+}
+
+/* The same K build with the distance-aware quartet test added to the keep rule
+ * (dist_tau > 0): ora_dist_estimate(I, J, K, L) >= dist_tau (symmetric in the eight
+ * orderings of the quartet). */
+double ora_build_K_dist(void *vs, const double *P, int mode, int nthreads, double dist_tau, double *Kout) {
+  ora_screen *s = (ora_screen *)vs;
+  s->dist_tau = dist_tau;
+  double e = ora_build_K(vs, P, mode, nthreads, Kout);
+  s->dist_tau = 0.0;
   return e;
 }
 

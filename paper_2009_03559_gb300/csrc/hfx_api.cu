@@ -1,6 +1,7 @@
 // C ABI of the HFX library: context, basis upload, pair-list build, K build.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -46,9 +47,19 @@ extern "C" void hfx_default_options(hfx_options* opt) {
   opt->fp32_class_mask = HFX_FP32_CLASSES_DEFAULT;
 }
 
+static int init_basis_impl(hfx_ctx** out, int n_atoms, const double* xyz, int n_shells, const int* shell_atom,
+                           const int* shell_l, const int* shell_nprim, const double* alpha, const double* coef,
+                           const hfx_options* opt, void* stream, bool periodic = false);
+
 extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int n_shells,
                               const int* shell_atom, const int* shell_l, const int* shell_nprim,
                               const double* alpha, const double* coef, const hfx_options* opt, void* stream) {
+  return init_basis_impl(out, n_atoms, xyz, n_shells, shell_atom, shell_l, shell_nprim, alpha, coef, opt, stream);
+}
+
+static int init_basis_impl(hfx_ctx** out, int n_atoms, const double* xyz, int n_shells, const int* shell_atom,
+                           const int* shell_l, const int* shell_nprim, const double* alpha, const double* coef,
+                           const hfx_options* opt, void* stream, bool periodic) {
   g_init_err.clear();
   if (!out) {
     g_init_err = "out is NULL";
@@ -63,7 +74,7 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
   hfx_default_options(&o);
   if (opt) o = *opt;
   if (!(o.omega >= 0.0) || !(o.schwarz_tau >= 0.0) || !(o.prim_tau >= 0.0) || !(o.fp32_tau >= 0.0) ||
-      !(o.density_tau >= 0.0) ||
+      !(o.density_tau >= 0.0) || !(o.dist_tau >= 0.0) ||
       (o.precision != HFX_FP64 && o.precision != HFX_MIXED) ||
       (o.fp32_pmax_global != 0 && o.fp32_pmax_global != 1) ||
       (o.schedule != HFX_SCHED_QUARTET && o.schedule != HFX_SCHED_PAIR && o.schedule != HFX_SCHED_DYNAMIC)) {
@@ -125,7 +136,7 @@ extern "C" int hfx_init_basis(hfx_ctx** out, int n_atoms, const double* xyz, int
       (r = ctx->alloc(&ctx->d_prim_off, n_shells)) || (r = ctx->alloc(&ctx->d_bf_off, n_shells)) ||
       (r = ctx->alloc(&ctx->d_energy, 1)) || (r = ctx->alloc(&ctx->d_busy, 1024)) ||
       (r = ctx->alloc(&ctx->d_counters, kNCnt * 21)) ||
-      (r = ctx->alloc(&ctx->d_pmax, (size_t)n_shells * n_shells)) || (r = ctx->alloc(&ctx->d_work, 64)) ||
+      (r = ctx->alloc(&ctx->d_pmax, periodic ? 1 : (size_t)n_shells * n_shells)) || (r = ctx->alloc(&ctx->d_work, 64)) ||
       (r = ctx->alloc(&ctx->d_pglob, 1)))
     return bail(r);
   ctx->n_part = 2 * ctx->n_sm;
@@ -208,7 +219,9 @@ extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   CK(cudaEventRecord(ctx->ev[44], s));
   const long long n = ctx->n_shells;
-  const long long n_tri = n * (n + 1) / 2;
+  // candidates: shell pairs I >= J (triangular index), or for a periodic context every
+  // (home-cell shell, image shell) pair (rectangular index)
+  const long long n_tri = ctx->periodic ? (long long)ctx->n_home_shells * n : n * (n + 1) / 2;
   // 1. candidate pairs passing the orbital cutoff
   int* d_flag;
   long long* d_cand_t;
@@ -216,7 +229,10 @@ extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
   RK(ctx->alloc(&d_flag, n_tri, true));
   RK(ctx->alloc(&d_cand_t, n_tri, true));
   RK(ctx->alloc(&d_num, 8, true));
-  CK(launch_pair_flags(n_tri, ctx->d_atom, ctx->d_xyz, ctx->opt.rcut_bohr, d_flag, s));
+  if (ctx->periodic)
+    CK(launch_pair_flags_rect(n_tri, (int)n, ctx->d_atom, ctx->d_xyz, ctx->opt.rcut_bohr, d_flag, s));
+  else
+    CK(launch_pair_flags(n_tri, ctx->d_atom, ctx->d_xyz, ctx->opt.rcut_bohr, d_flag, s));
   size_t tb = 0;
   CK(select_flagged(nullptr, tb, n_tri, d_flag, d_cand_t, d_num, s));
   void* tmp;
@@ -250,8 +266,14 @@ extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
   RK(ctx->alloc(&ctx->d_pp_off, n_cand, true));
   RK(ctx->alloc(&ctx->d_pp_n, n_cand, true));
   RK(ctx->alloc(&ctx->d_Q, n_cand, true));
-  CK(launch_pair_setup(n_cand, d_cand_t, ctx->d_l, ctx->d_nprim, ctx->d_atom, ctx->d_xyz, ctx->d_sa, ctx->d_sb,
-                       ctx->d_pcls, ctx->d_AB, d_cap, s));
+  if (ctx->periodic) {
+    RK(ctx->alloc(&ctx->d_home_first, n_cand, true));
+    CK(launch_pair_setup_rect(n_cand, d_cand_t, (int)n, ctx->d_l, ctx->d_nprim, ctx->d_atom, ctx->d_xyz, ctx->d_sa,
+                              ctx->d_sb, ctx->d_pcls, ctx->d_AB, d_cap, ctx->d_home_first, s));
+  } else {
+    CK(launch_pair_setup(n_cand, d_cand_t, ctx->d_l, ctx->d_nprim, ctx->d_atom, ctx->d_xyz, ctx->d_sa, ctx->d_sb,
+                         ctx->d_pcls, ctx->d_AB, d_cap, s));
+  }
   tb = tmp_bytes;
   CK(scan_int(tmp, tb, d_cap, ctx->d_pp_off, n_cand, s));
   int last[2];
@@ -326,6 +348,14 @@ extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
   ctx->n_kept = acc;
   RK(ctx->alloc(&ctx->d_Qs, std::max(1, acc), true));
   CK(launch_gather_q(acc, ctx->d_sorted, ctx->d_Q, ctx->d_Qs, s));
+  if (ctx->opt.dist_tau > 0.0) {
+    double* d_dc;
+    RK(ctx->alloc(&d_dc, 5 * (size_t)n_cand, true));
+    RK(ctx->alloc(&ctx->d_dist, 5 * (size_t)std::max(1, acc), true));
+    CK(launch_pair_dist(n_cand, ctx->d_sa, ctx->d_sb, ctx->d_nprim, ctx->d_prim_off, ctx->d_atom, ctx->d_xyz,
+                        ctx->d_alpha, d_dc, s));
+    CK(launch_gather5(acc, ctx->d_sorted, d_dc, ctx->d_dist, s));
+  }
   // 5. quartet task rows and prefix sums
   int rows = 0;
   for (int cp = 0; cp < 21; ++cp) {
@@ -341,7 +371,7 @@ extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
   RK(ctx->alloc(&d_rown, std::max(1, rows), true));
   RK(ctx->alloc(&ctx->d_qoff, (size_t)rows + 1, true));
   RK(ctx->alloc(&d_bounds, 32, true));
-  CK(launch_count(rows, rt, ctx->d_Qs, ctx->opt.schwarz_tau, d_rown, s));
+  CK(launch_count(rows, rt, ctx->d_Qs, ctx->opt.schwarz_tau, d_rown, s, !ctx->periodic));
   CK(cudaMemsetAsync(ctx->d_qoff, 0, sizeof(long long), s));
   if (rows > 0) {
     tb = tmp_bytes;
@@ -365,6 +395,221 @@ extern "C" int hfx_build_pairs(hfx_ctx* ctx) {
   ctx->stats.n_quartets = total;
   ctx->stats.ms_pairs = ctx->ms_pairs;
   ctx->pairs_ready = true;
+  return HFX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Periodic images (Eq. vx lattice sums)
+// ---------------------------------------------------------------------------
+extern "C" int hfx_init_periodic(hfx_ctx** out, int n_atoms, const double* xyz, const double* lattice, int n_shells,
+                                 const int* shell_atom, const int* shell_l, const int* shell_nprim,
+                                 const double* alpha, const double* coef, const hfx_options* opt, void* stream) {
+  g_init_err.clear();
+  if (!out || !lattice || n_atoms <= 0 || n_shells <= 0 || !xyz || !shell_atom || !shell_nprim || !alpha || !coef) {
+    g_init_err = "NULL argument or empty cell";
+    if (out) *out = nullptr;
+    return HFX_ERR_ARG;
+  }
+  *out = nullptr;
+  hfx_options o;
+  hfx_default_options(&o);
+  if (opt) o = *opt;
+  if (!(o.rcut_bohr > 0.0)) {
+    g_init_err = "a periodic context needs an orbital cutoff (rcut_bohr > 0): it bounds the image sums";
+    return HFX_ERR_ARG;
+  }
+  if (o.precision != HFX_FP64) {
+    g_init_err = "periodic builds run in FP64";
+    return HFX_ERR_ARG;
+  }
+  // box of image cells: every cell whose atoms can come within 2 r_c of a home-cell atom
+  const double* L = lattice;
+  double diam = 0.0;
+  for (int a = 0; a < n_atoms; ++a)
+    for (int b = 0; b < n_atoms; ++b) {
+      double d2 = 0.0;
+      for (int i = 0; i < 3; ++i) d2 += (xyz[3 * a + i] - xyz[3 * b + i]) * (xyz[3 * a + i] - xyz[3 * b + i]);
+      diam = std::max(diam, std::sqrt(d2));
+    }
+  auto cross = [](const double* u, const double* v, double* w) {
+    w[0] = u[1] * v[2] - u[2] * v[1];
+    w[1] = u[2] * v[0] - u[0] * v[2];
+    w[2] = u[0] * v[1] - u[1] * v[0];
+  };
+  double c01[3], c12[3], c20[3];
+  cross(L + 0, L + 3, c01);
+  cross(L + 3, L + 6, c12);
+  cross(L + 6, L + 0, c20);
+  const double vol = std::fabs(L[0] * c12[0] + L[1] * c12[1] + L[2] * c12[2]);
+  if (!(vol > 0.0) || !std::isfinite(vol)) {
+    g_init_err = "lattice vectors are degenerate";
+    return HFX_ERR_ARG;
+  }
+  int nr[3];
+  const double* cr[3] = {c12, c20, c01};  // normals of the faces spanned by the other two vectors
+  for (int i = 0; i < 3; ++i) {
+    const double h = vol / std::sqrt(cr[i][0] * cr[i][0] + cr[i][1] * cr[i][1] + cr[i][2] * cr[i][2]);
+    nr[i] = (int)std::ceil((2.0 * o.rcut_bohr + diam) / h);
+    if (nr[i] > 8) {
+      g_init_err = "orbital cutoff reaches more than 8 cells: use a larger cell";
+      return HFX_ERR_ARG;
+    }
+  }
+  std::vector<int> cells = {0, 0, 0};
+  for (int i = -nr[0]; i <= nr[0]; ++i)
+    for (int j = -nr[1]; j <= nr[1]; ++j)
+      for (int k = -nr[2]; k <= nr[2]; ++k)
+        if (i || j || k) cells.insert(cells.end(), {i, j, k});
+  const int nc = (int)cells.size() / 3;
+  // the image cluster: the cell's atoms and shells repeated cell after cell
+  std::vector<double> cx((size_t)3 * n_atoms * nc), ca, cc;
+  std::vector<int> csa((size_t)n_shells * nc), csl((size_t)n_shells * nc), csn((size_t)n_shells * nc);
+  int np = 0;
+  for (int sh = 0; sh < n_shells; ++sh) np += shell_nprim[sh];
+  ca.reserve((size_t)np * nc);
+  cc.reserve((size_t)np * nc);
+  for (int c = 0; c < nc; ++c) {
+    const int* n3 = &cells[3 * c];
+    for (int a = 0; a < n_atoms; ++a)
+      for (int i = 0; i < 3; ++i)
+        cx[(size_t)3 * (c * n_atoms + a) + i] = xyz[3 * a + i] + n3[0] * L[i] + n3[1] * L[3 + i] + n3[2] * L[6 + i];
+    for (int sh = 0; sh < n_shells; ++sh) {
+      csa[(size_t)c * n_shells + sh] = shell_atom[sh] + c * n_atoms;
+      csl[(size_t)c * n_shells + sh] = shell_l[sh];
+      csn[(size_t)c * n_shells + sh] = shell_nprim[sh];
+    }
+    ca.insert(ca.end(), alpha, alpha + np);
+    cc.insert(cc.end(), coef, coef + np);
+  }
+  int r = init_basis_impl(out, n_atoms * nc, cx.data(), n_shells * nc, csa.data(), csl.data(), csn.data(), ca.data(),
+                          cc.data(), &o, stream, true);
+  if (r != HFX_OK) return r;
+  hfx_ctx* ctx = *out;
+  ctx->periodic = true;
+  ctx->n_home_atoms = n_atoms;
+  ctx->n_home_shells = n_shells;
+  ctx->n_home_bf = ctx->n_bf / nc;
+  ctx->n_cells = nc;
+  std::memcpy(ctx->lattice, lattice, sizeof(ctx->lattice));
+  ctx->h_cells = cells;
+  std::vector<int> shell_cell((size_t)n_shells * nc), shell_bf((size_t)n_shells * nc);
+  int bf = 0;
+  for (int sh = 0; sh < n_shells; ++sh) {
+    for (int c = 0; c < nc; ++c) {
+      shell_cell[(size_t)c * n_shells + sh] = c;
+      shell_bf[(size_t)c * n_shells + sh] = bf;
+    }
+    bf += 2 * shell_l[sh] + 1;
+  }
+  auto bail = [&](int code) {
+    g_init_err = ctx->err;
+    hfx_free(ctx);
+    *out = nullptr;
+    return code;
+  };
+  if ((r = ctx->alloc(&ctx->d_shell_cell, shell_cell.size())) || (r = ctx->alloc(&ctx->d_shell_bf, shell_bf.size())) ||
+      (r = ctx->alloc(&ctx->d_cell_xyz, cells.size())))
+    return bail(r);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(ctx->d_shell_cell, shell_cell.data(), sizeof(int) * shell_cell.size(),
+                           cudaMemcpyHostToDevice, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(ctx->d_shell_bf, shell_bf.data(), sizeof(int) * shell_bf.size(), cudaMemcpyHostToDevice,
+                           ctx->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(ctx->d_cell_xyz, cells.data(), sizeof(int) * cells.size(), cudaMemcpyHostToDevice,
+                           ctx->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+    return bail(ctx->cuda_fail("periodic tables", e));
+  return HFX_OK;
+}
+
+extern "C" int hfx_periodic_cells(const hfx_ctx* ctx, int* cells, int max_n) {
+  if (!ctx || !ctx->periodic) return HFX_ERR_ARG;
+  if (cells) std::memcpy(cells, ctx->h_cells.data(), sizeof(int) * 3 * std::min(max_n, ctx->n_cells));
+  return ctx->n_cells;
+}
+
+extern "C" int hfx_build_K_periodic(hfx_ctx* ctx, int n_R, const int* R_cells, const double* P_R, int n_G,
+                                    const int* G_cells, double* K_G) {
+  if (!ctx) return HFX_ERR_ARG;
+  if (!ctx->periodic) return ctx->fail(HFX_ERR_STATE, "hfx_build_K_periodic needs a context from hfx_init_periodic");
+  if (!ctx->pairs_ready) return ctx->fail(HFX_ERR_STATE, "hfx_build_K_periodic before hfx_build_pairs");
+  if (n_R <= 0 || n_G <= 0 || !R_cells || !P_R || !G_cells || !K_G)
+    return ctx->fail(HFX_ERR_ARG, "empty or NULL density or cell lists");
+  int rb = 0;
+  for (int i = 0; i < 3 * n_R; ++i) rb = std::max(rb, std::abs(R_cells[i]));
+  if (rb > 32) return ctx->fail(HFX_ERR_ARG, "density cell offsets beyond 32 cells");
+  const int w = 2 * rb + 1;
+  std::vector<int> rmap((size_t)w * w * w, -1);
+  for (int r = 0; r < n_R; ++r) {
+    const int* R = R_cells + 3 * r;
+    int& slot = rmap[((size_t)(R[0] + rb) * w + (R[1] + rb)) * w + (R[2] + rb)];
+    if (slot >= 0) return ctx->fail(HFX_ERR_ARG, "a density cell offset appears twice");
+    slot = r;
+  }
+  cudaStream_t s = ctx->stream;
+  const int nbf = ctx->n_home_bf;
+  int* d_rmap = nullptr;
+  RK(ctx->alloc(&d_rmap, rmap.size(), true));
+  CK(cudaMemcpyAsync(d_rmap, rmap.data(), sizeof(int) * rmap.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(K_G, 0, sizeof(double) * (size_t)n_G * nbf * nbf, s));
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], s));
+  EriLaunch L = base_launch(ctx);
+  L.sorted = ctx->d_sorted;
+  L.qoff = ctx->d_qoff;
+  L.Qs = ctx->d_Qs;
+  L.per.shell_cell = ctx->d_shell_cell;
+  L.per.shell_bf = ctx->d_shell_bf;
+  L.per.cell_xyz = ctx->d_cell_xyz;
+  L.per.home_first = ctx->d_home_first;
+  L.per.rmap = d_rmap;
+  L.per.rb = rb;
+  L.per.P = P_R;
+  L.per.nbf = nbf;
+  L.schedule = HFX_SCHED_DYNAMIC;
+  for (int g = 0; g < n_G; ++g) {
+    const int* G = G_cells + 3 * g;
+    // K^{-G} = (K^G)^T (exchanging bra and ket pairs maps the quartets of cell G onto those of
+    // cell -G): a cell whose opposite came earlier in the list is a transpose
+    int mirror = -1;
+    for (int j = 0; j < g && mirror < 0; ++j)
+      if (G_cells[3 * j] == -G[0] && G_cells[3 * j + 1] == -G[1] && G_cells[3 * j + 2] == -G[2]) mirror = j;
+    if (mirror >= 0) {
+      CK(launch_transpose(nbf, K_G + (size_t)mirror * nbf * nbf, K_G + (size_t)g * nbf * nbf, s));
+      continue;
+    }
+    double sh[3];
+    for (int i = 0; i < 3; ++i)
+      sh[i] = G[0] * ctx->lattice[i] + G[1] * ctx->lattice[3 + i] + G[2] * ctx->lattice[6 + i];
+    L.KG = K_G + (size_t)g * nbf * nbf;
+    CK(cudaMemsetAsync(ctx->d_work, 0, 64 * sizeof(unsigned long long), s));
+    for (int cp = 0; cp < 21; ++cp) {
+      if (ctx->cls_q[cp] == 0) continue;
+      int hi = 0;
+      while ((hi + 1) * (hi + 2) / 2 <= cp) ++hi;
+      const int lo = cp - hi * (hi + 1) / 2;
+      L.ci = class_info_host()[cp];
+      L.row_begin = ctx->rt.row_base[cp];
+      L.row_end = ctx->rt.row_base[cp + 1];
+      L.bra_bin_start = ctx->rt.bin_start[hi];
+      L.ket_bin_start = ctx->rt.bin_start[lo];
+      L.q_begin = ctx->cls_qbegin[cp];
+      L.q_count = ctx->cls_q[cp];
+      const int gs = eri_group_size(cp);
+      L.chunk = gs == 1 ? 256 : 8;
+      // forward: (p | q + G L) for bra class hi >= ket class lo; reverse (hi > lo): the
+      // quartets (p | q + G L) with class(p) = lo < class(q) = hi, evaluated as (q | p - G L)
+      for (int rev = 0; rev < (hi > lo ? 2 : 1); ++rev) {
+        L.reverse = rev;
+        for (int i = 0; i < 3; ++i) {
+          L.gcell[i] = G[i];
+          L.shift[i] = rev ? -sh[i] : sh[i];
+        }
+        L.work = ctx->d_work + cp + 21 * rev;
+        CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, L.q_count, gs, 3), s, gs, 3, false));
+      }
+    }
+  }
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], s));
   return HFX_OK;
 }
 
@@ -396,6 +641,7 @@ extern "C" int hfx_build_K_part(hfx_ctx* ctx, const double* P, double* K, int ld
 
 static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int part, int n_parts) {
   if (!ctx) return HFX_ERR_ARG;
+  if (ctx->periodic) return ctx->fail(HFX_ERR_STATE, "a periodic context builds K with hfx_build_K_periodic");
   if (!ctx->pairs_ready) return ctx->fail(HFX_ERR_STATE, "hfx_build_K before hfx_build_pairs");
   if (!P || !K || ld < ctx->n_bf) return ctx->fail(HFX_ERR_ARG, "NULL matrix or ld < n_bf");
   cudaStream_t s = ctx->stream;
@@ -427,6 +673,8 @@ static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int pa
   L.skip_zero = ctx->opt.skip_zero_p;
   L.fp32_tau = ctx->opt.fp32_tau;
   L.dens_tau = ctx->opt.density_tau;
+  L.dist_tau = ctx->opt.dist_tau;
+  L.dist = ctx->d_dist;
   L.Qs = ctx->d_Qs;
   if (ctx->timing) L.busy = ctx->d_busy;
   for (int cp = 0; cp < 21; ++cp) {

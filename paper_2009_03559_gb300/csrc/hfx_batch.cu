@@ -135,6 +135,8 @@ void bw_fill(BatchWork& w, hfx_ctx* const* ctxs, int n, double* const* pmax, dou
       L.fp32_tau = c->opt.fp32_tau;
       L.pglob = glob ? pglob[s] : nullptr;
       L.dens_tau = c->opt.density_tau;
+      L.dist_tau = c->opt.dist_tau;
+      L.dist = c->d_dist;
       L.Qs = c->d_Qs;
       w.h_launch[(size_t)cp * w.cap + s] = L;
     }

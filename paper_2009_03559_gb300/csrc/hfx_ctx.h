@@ -24,6 +24,7 @@ struct hfx_ctx {
   int n_cand = 0, n_kept = 0;
   int *d_sa = nullptr, *d_sb = nullptr, *d_pcls = nullptr, *d_pp_off = nullptr, *d_pp_n = nullptr;
   double *d_AB = nullptr, *d_Q = nullptr, *d_Qs = nullptr;
+  double* d_dist = nullptr;  // distance-aware test data per sorted pair (5 doubles)
   hfx::PrimPair* d_pp = nullptr;
   int* d_sorted = nullptr;
   hfx::RowTable rt{};
@@ -47,6 +48,14 @@ struct hfx_ctx {
   int streams_override[21] = {};  // warp kernel: primitive quartets at a time (0 = default)
   int streams_used[21] = {};
   hfx_stats stats{};
+  // periodic context (hfx_init_periodic): the basis above is the image cluster, the home
+  // cell's shells repeated over n_cells cells (home cell first)
+  bool periodic = false;
+  int n_home_atoms = 0, n_home_shells = 0, n_home_bf = 0, n_cells = 0;
+  double lattice[9] = {};
+  std::vector<int> h_cells;              // 3 per cell
+  int *d_shell_cell = nullptr, *d_shell_bf = nullptr, *d_cell_xyz = nullptr;
+  unsigned char* d_home_first = nullptr;  // per candidate pair (pair scope)
   float ms_pairs = 0.f;
   std::vector<void*> allocs;       // owned for the context lifetime
   std::vector<void*> pair_allocs;  // owned until the next build_pairs

@@ -21,7 +21,7 @@ const EriClassInfo* class_info_host() { return kClassInfo; }
 // of the thread's own FP64 slot k (so no other lane's slots are ever touched); the
 // accumulated block is then widened in place into the FP64 slots Sd, where the horizontal
 // recurrences and the spherical step run.  R = double: the FP64 slots themselves.
-template <typename R>
+template <typename R, bool PER = false>
 __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaunch& L, int bra, int ket, double* Sd,
                                            int st) {
   R* S = reinterpret_cast<R*>(Sd);
@@ -42,7 +42,12 @@ __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaun
     const int ib = t / nk, ik = t - ib * nk;
     {
       const PrimPair b = pb[ib];
-      const PrimPair k = pk[ik];
+      PrimPair k = pk[ik];
+      if constexpr (PER) {  // the ket pair's image in cell G (its centre moves, P - C does not)
+        k.P[0] += L.shift[0];
+        k.P[1] += L.shift[1];
+        k.P[2] += L.shift[2];
+      }
       CoefRg c;
       double Gm[kMaxLt + 1];
       if (!prim_setup(b, k, ci.E, ci.F, ci.Lt, omega, omega2, boys, c, Gm)) continue;
@@ -119,7 +124,7 @@ __host__ __device__ __forceinline__ int g32_stride(const SchedVariant& sv) {
   return sv.group + 33 * HFX_NCOEF + 1;
 }
 
-template <typename R>
+template <typename R, bool PER = false>
 __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedVariant& sv, const EriLaunch& L,
                                             int bra, int ket, R* S, R* CF, int lane) {
   const PairArrays pa = L.pa;
@@ -149,7 +154,13 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedV
     if (t < npq) {
       ib = t / nk;
       ik = t - ib * nk;
-      ok = prim_core(pb[ib], pk[ik], ci.Lt, omega, omega2, boys, G, ps);
+      PrimPair k = pk[ik];
+      if constexpr (PER) {  // the ket pair's image in cell G
+        k.P[0] += L.shift[0];
+        k.P[1] += L.shift[1];
+        k.P[2] += L.shift[2];
+      }
+      ok = prim_core(pb[ib], k, ci.Lt, omega, omega2, boys, G, ps);
     }
     const unsigned okm = __ballot_sync(0xffffffffu, ok);
     if (ok)
@@ -293,7 +304,8 @@ __device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const Sch
 
 // Precision passes of a class launch: 0 every quartet in FP64; 1 (mixed precision, first
 // pass) the quartets that must stay FP64; 2 (second pass) those whose recurrences run in FP32.
-enum { PREC_FP64 = 0, PREC_MIXED64 = 1, PREC_MIXED32 = 2 };
+// PREC_PERIODIC: the FP64 periodic instance (quartets of the lattice sums, see per_quartet).
+enum { PREC_FP64 = 0, PREC_MIXED64 = 1, PREC_MIXED32 = 2, PREC_PERIODIC = 3 };
 
 // The digest reads P_bd, P_bc, P_ad, P_ac.  max of their max|P| (or 1 without the table):
 // 0 means the quartet contributes exactly nothing; the mixed-precision and the
@@ -304,6 +316,20 @@ __device__ __forceinline__ double pmax4(const EriLaunch& L, int sa, int sb, int 
   const size_t ns = L.ns;
   return fmax(fmax(__ldg(pm + sb * ns + sd), __ldg(pm + sb * ns + sc)),
               fmax(__ldg(pm + sa * ns + sd), __ldg(pm + sa * ns + sc)));
+}
+
+// Distance-aware test: Q_IJ Q_KL exp(-kappa rho R^2) >= dist_tau (see hfx_options.dist_tau).
+__device__ __forceinline__ bool dist_keeps(const EriLaunch& Ls, int bra_s, int ket_s) {
+  if (!(Ls.dist_tau > 0.0)) return true;
+  const double* a = Ls.dist + 5 * (size_t)bra_s;
+  const double* b = Ls.dist + 5 * (size_t)ket_s;
+  const double dx = __ldg(a) - __ldg(b), dy = __ldg(a + 1) - __ldg(b + 1), dz = __ldg(a + 2) - __ldg(b + 2);
+  double r = sqrt(dx * dx + dy * dy + dz * dz) - __ldg(a + 3) - __ldg(b + 3);
+  if (r < 0.0) r = 0.0;
+  const double p = __ldg(a + 4), q = __ldg(b + 4);
+  const double rho = p * q / (p + q);
+  const double lam = Ls.omega2 * rho / (Ls.omega2 + rho);
+  return __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * exp(-lam * r * r) >= Ls.dist_tau;
 }
 
 // Mixed precision: FP32 recurrences for the quartet when the class allows it and its
@@ -331,6 +357,75 @@ __device__ __forceinline__ void record_busy(const EriLaunch& L, unsigned long lo
   }
 }
 
+// ---------------------------------------------------------------------------
+// Periodic quartets (Eq. vx with lattice images): the launch for cell G evaluates
+// (X | Y + shift) for bra pair X and ket pair Y of the home-anchored pair list and adds
+//   K^G_{ab} += sum_{c,d} (a c | b d) P^{R}_{cd},   R = cell(d) - cell(c),
+// where a is the home-cell shell of the pair holding the row function (X for a forward
+// launch, Y for a reverse one), c its partner, b the home-cell shell of the other pair
+// (in cell G) and d its partner.  Every ordered pair of pairs is one quartet (no
+// permutational symmetry is used across cells), so the degeneracy factor is 1.
+// ---------------------------------------------------------------------------
+struct PerQuartet {
+  int pa, pb, pc, pd;        // positions of shells a, b, c, d in the quartet block (x1 x2 y1 y2)
+  int bfa, bfb, bfc, bfd;    // their first functions (home-cell numbering)
+  const double* PR;          // density block P^R
+};
+
+__device__ __forceinline__ bool per_quartet(const EriLaunch& L, int bra, int ket, PerQuartet& q) {
+  const PeriodicInfo& pi = L.per;
+  const int sax = __ldg(L.pa.sa + bra), sbx = __ldg(L.pa.sb + bra);
+  const int say = __ldg(L.pa.sa + ket), sby = __ldg(L.pa.sb + ket);
+  const bool hx = __ldg(pi.home_first + bra), hy = __ldg(pi.home_first + ket);
+  const int hxs = hx ? sax : sbx, oxs = hx ? sbx : sax;
+  const int hys = hy ? say : sby, oys = hy ? sby : say;
+  const int* cx = pi.cell_xyz + 3 * __ldg(pi.shell_cell + oxs);
+  const int* cy = pi.cell_xyz + 3 * __ldg(pi.shell_cell + oys);
+  const int w = 2 * pi.rb + 1;
+  int idx = 0;
+  for (int i = 0; i < 3; ++i) {
+    const int d = __ldg(cy + i) - __ldg(cx + i);
+    const int R = L.gcell[i] + (L.reverse ? -d : d);
+    if (R < -pi.rb || R > pi.rb) return false;
+    idx = idx * w + (R + pi.rb);
+  }
+  const int blk = __ldg(pi.rmap + idx);
+  if (blk < 0) return false;
+  q.PR = pi.P + (size_t)blk * pi.nbf * pi.nbf;
+  const int phx = hx ? 0 : 1, pox = 1 - phx, phy = hy ? 2 : 3, poy = 5 - phy;
+  if (!L.reverse) {
+    q.pa = phx; q.pc = pox; q.pb = phy; q.pd = poy;
+    q.bfa = __ldg(pi.shell_bf + hxs); q.bfc = __ldg(pi.shell_bf + oxs);
+    q.bfb = __ldg(pi.shell_bf + hys); q.bfd = __ldg(pi.shell_bf + oys);
+  } else {
+    q.pa = phy; q.pc = poy; q.pb = phx; q.pd = pox;
+    q.bfa = __ldg(pi.shell_bf + hys); q.bfc = __ldg(pi.shell_bf + oys);
+    q.bfb = __ldg(pi.shell_bf + hxs); q.bfd = __ldg(pi.shell_bf + oxs);
+  }
+  return true;
+}
+
+// K^G_{ab} += sum_{cd} v P^R_{cd} for the final block v (stride st); outputs o0, o0 + ostep, ...
+__device__ __forceinline__ void digest_per(const EriClassInfo& ci, const double* v, int st, const PerQuartet& q,
+                                           double* KG, int nbf, int o0, int ostep) {
+  int str[4];
+  str[3] = 1;
+  str[2] = ci.dims[3];
+  str[1] = ci.dims[2] * str[2];
+  str[0] = ci.dims[1] * str[1];
+  const int na = ci.dims[q.pa], nb = ci.dims[q.pb], nc = ci.dims[q.pc], nd = ci.dims[q.pd];
+  const int sa = str[q.pa], sb = str[q.pb], sc = str[q.pc], sd = str[q.pd];
+  for (int o = o0; o < na * nb; o += ostep) {
+    const int ia = o / nb, ib = o - ia * nb;
+    double acc = 0.0;
+    for (int ic = 0; ic < nc; ++ic)
+      for (int id = 0; id < nd; ++id)
+        acc = fma(v[(ia * sa + ib * sb + ic * sc + id * sd) * st], __ldg(q.PR + (size_t)(q.bfc + ic) * nbf + q.bfd + id),
+                  acc);
+    atomicAdd(KG + (size_t)(q.bfa + ia) * nbf + q.bfb + ib, acc);
+  }
+}
+
 // Per-thread tallies of one kernel, added to the launch's counters once at the end.
 struct Tally {
   unsigned long long prim = 0, quart = 0, skip = 0, q32 = 0, p32 = 0;
@@ -338,10 +433,22 @@ struct Tally {
 
 // One quartet evaluated and digested by one lane (one quartet per thread), recurrences in
 // precision R; Sd: the thread's FP64 slots.
-template <typename R>
+template <typename R, bool PER = false>
 __device__ __forceinline__ void g1_quartet(const EriClassInfo& ci, const EriLaunch& Ls, int bra_s, int ket_s,
                                            double* Sd, int st, Tally& t) {
   const int bra = __ldg(Ls.sorted + bra_s), ket = __ldg(Ls.sorted + ket_s);
+  if constexpr (PER) {
+    PerQuartet pq;
+    if (!per_quartet(Ls, bra, ket, pq)) return;
+    const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
+    const int ne = contract_g1<double, true>(ci, Ls, bra, ket, Sd, st);
+    t.prim += ne;
+    t.skip += npq - ne;
+    if (!ne) return;
+    ++t.quart;
+    digest_per(ci, Sd + ci.out_base * st, st, pq, Ls.KG, Ls.per.nbf, 0, 1);
+    return;
+  }
   const int sa = __ldg(Ls.pa.sa + bra), sb = __ldg(Ls.pa.sb + bra);
   const int sc = __ldg(Ls.pa.sa + ket), sd = __ldg(Ls.pa.sb + ket);
   const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
@@ -396,7 +503,7 @@ __device__ __forceinline__ void sort64_desc(int& k0, int& k1, int lane) {
   }
 }
 
-template <bool BATCH, typename R>
+template <bool BATCH, typename R, bool PER = false>
 __device__ __forceinline__ void g1_drain(const EriLaunch& L, const EriClassInfo& ci, G1Queue& Q, int lane,
                                          double* Sd, int st, Tally& t, bool all) {
   while (Q.n >= 32 || (all && Q.n > 0)) {
@@ -419,13 +526,13 @@ __device__ __forceinline__ void g1_drain(const EriLaunch& L, const EriClassInfo&
     }
     __syncwarp();
     Q.n -= take;
-    if (lane < take) g1_quartet<R>(ci, BATCH ? L.batch[e.x] : L, e.y, e.z, Sd, st, t);
+    if (lane < take) g1_quartet<R, PER>(ci, BATCH ? L.batch[e.x] : L, e.y, e.z, Sd, st, t);
   }
 }
 
 // Quartets [q0, q1) of the launch record Ls (system sys), one quartet per thread: the warp
 // tests 32 consecutive quartets at a time and queues the survivors.
-template <bool BATCH, int PREC, typename R>
+template <bool BATCH, int PREC, typename R, bool PER = false>
 __device__ __forceinline__ void g1_range(const EriLaunch& L, const EriClassInfo& ci, const EriLaunch& Ls, int sys,
                                          long long q0, long long q1, double* Sd, int st, int lane, G1Queue& Q,
                                          Tally& t) {
@@ -444,17 +551,22 @@ __device__ __forceinline__ void g1_range(const EriLaunch& L, const EriClassInfo&
       bra_s = bra0 + (r - row_begin);
       ket_s = ket0 + (int)(q - __ldg(qoff + r));
       const int bra = __ldg(Ls.sorted + bra_s), ket = __ldg(Ls.sorted + ket_s);
-      const double pm = pmax4(Ls, __ldg(Ls.pa.sa + bra), __ldg(Ls.pa.sb + bra), __ldg(Ls.pa.sa + ket),
-                              __ldg(Ls.pa.sb + ket));
-      keep = !(skip && pm == 0.0) && !(dens > 0.0 && __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pm < dens) &&
-             pass_takes<PREC>(Ls, bra_s, ket_s, pm);
+      if constexpr (PER) {
+        PerQuartet pq;
+        keep = per_quartet(Ls, bra, ket, pq);  // a density block exists for its cell offset
+      } else {
+        const double pm = pmax4(Ls, __ldg(Ls.pa.sa + bra), __ldg(Ls.pa.sb + bra), __ldg(Ls.pa.sa + ket),
+                                __ldg(Ls.pa.sb + ket));
+        keep = !(skip && pm == 0.0) && !(dens > 0.0 && __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pm < dens) &&
+               dist_keeps(Ls, bra_s, ket_s) && pass_takes<PREC>(Ls, bra_s, ket_s, pm);
+      }
       npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
     }
     const unsigned m = __ballot_sync(0xffffffffu, keep);
     if (keep) Q.q[Q.n + __popc(m & ((1u << lane) - 1u))] = make_int4(sys, bra_s, ket_s, npq);
     Q.n += __popc(m);
     __syncwarp();
-    g1_drain<BATCH, R>(L, ci, Q, lane, Sd, st, t, false);
+    g1_drain<BATCH, R, PER>(L, ci, Q, lane, Sd, st, t, false);
   }
 }
 
@@ -476,6 +588,8 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const SchedVar
     if (Ls.skip_zero && pm == 0.0) continue;
     // density-weighted screening (off when dens_tau = 0)
     if (Ls.dens_tau > 0.0 && __ldg(Ls.Qs + bra_s) * __ldg(Ls.Qs + ket_s) * pm < Ls.dens_tau) continue;
+    // distance-aware screening (off when dist_tau = 0)
+    if (!dist_keeps(Ls, bra_s, ket_s)) continue;
     // mixed precision: this pass's share of the quartets (warp-uniform decision)
     if (!pass_takes<PREC>(Ls, bra_s, ket_s, pm)) continue;
     const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
@@ -501,6 +615,29 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const SchedVar
     const int C = __ldg(Ls.sh.bf_off + sc), D = __ldg(Ls.sh.bf_off + sd);
     // an FP32 quartet leaves its final block in FP64 too (see contract_g32)
     digest(ci, S + ci.out_base, 1, A, B, C, D, deg, Ls.P, Ls.K, Ls.ld, lane, 32);
+    __syncwarp();
+  }
+}
+
+// Periodic quartets [q0, q1) of the launch (FP64), one warp per quartet.
+__device__ __forceinline__ void g32_range_per(const EriClassInfo& ci, const SchedVariant& sv, const EriLaunch& Ls,
+                                              long long q0, long long q1, double* S, double* CF, int lane, Tally& t) {
+  if (q0 >= q1) return;
+  int r = find_row(Ls.qoff, Ls.row_begin, Ls.row_end, q0);
+  for (long long q = q0; q < q1; ++q) {
+    while (__ldg(Ls.qoff + r + 1) <= q) ++r;
+    const int bra_s = Ls.bra_bin_start + (r - Ls.row_begin);
+    const int ket_s = Ls.ket_bin_start + (int)(q - __ldg(Ls.qoff + r));
+    const int bra = __ldg(Ls.sorted + bra_s), ket = __ldg(Ls.sorted + ket_s);
+    PerQuartet pq;
+    if (!per_quartet(Ls, bra, ket, pq)) continue;
+    const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
+    const int ne = contract_g32<double, true>(ci, sv, Ls, bra, ket, S, CF, lane);
+    t.prim += ne;
+    t.skip += npq - ne;
+    if (!ne) continue;
+    ++t.quart;
+    digest_per(ci, S + ci.out_base, 1, pq, Ls.KG, Ls.per.nbf, lane, 32);
     __syncwarp();
   }
 }
@@ -553,7 +690,7 @@ __device__ __forceinline__ void flush_tally(const EriLaunch& L, const Tally& t) 
   atomicAdd(L.counters + 4, t.p32);
 }
 
-template <int MODE, int PREC, bool BATCH>
+template <int MODE, int PREC, bool BATCH, bool PER = false>
 __global__ void __launch_bounds__(64, (BATCH || PREC == PREC_MIXED32) ? HFX_G1B_MINB : HFX_G1_MINB)
     eri_g1_kernel(const EriLaunch L) {
   extern __shared__ double smem[];
@@ -570,9 +707,9 @@ __global__ void __launch_bounds__(64, (BATCH || PREC == PREC_MIXED32) ? HFX_G1B_
     G1Queue Q{reinterpret_cast<int4*>(smem + (size_t)L.ci.scratch * blockDim.x) + (threadIdx.x >> 5) * 64, 0};
     for_each_range<BATCH, 32>(L, gid >> 5, ng >> 5, lane, 0xffffffffu,
                               [&](const EriLaunch& Ls, int sys, long long q0, long long q1) {
-                                g1_range<BATCH, PREC, R>(L, L.ci, Ls, sys, q0, q1, Sd, st, lane, Q, t);
+                                g1_range<BATCH, PREC, R, PER>(L, L.ci, Ls, sys, q0, q1, Sd, st, lane, Q, t);
                               });
-    g1_drain<BATCH, R>(L, L.ci, Q, lane, Sd, st, t, true);
+    g1_drain<BATCH, R, PER>(L, L.ci, Q, lane, Sd, st, t, true);
     flush_tally(L, t);
   } else {
     for (long long t = gid; t < L.diag_n; t += ng) {
@@ -585,7 +722,7 @@ __global__ void __launch_bounds__(64, (BATCH || PREC == PREC_MIXED32) ? HFX_G1B_
   record_busy(L, t0);
 }
 
-template <int MODE, int PREC, bool BATCH>
+template <int MODE, int PREC, bool BATCH, bool PER = false>
 __global__ void __launch_bounds__(64, BATCH ? HFX_G32B_MINB : HFX_G32_MINB) eri_g32_kernel(const EriLaunch L) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
@@ -600,7 +737,10 @@ __global__ void __launch_bounds__(64, BATCH ? HFX_G32B_MINB : HFX_G32_MINB) eri_
     Tally t;
     for_each_range<BATCH, 32>(L, gid, ng, lane, 0xffffffffu,
                               [&](const EriLaunch& Ls, int, long long q0, long long q1) {
-                                g32_range<PREC>(L.ci, L.sv, Ls, q0, q1, S, CF, lane, t);
+                                if constexpr (PER)
+                                  g32_range_per(L.ci, L.sv, Ls, q0, q1, S, CF, lane, t);
+                                else
+                                  g32_range<PREC>(L.ci, L.sv, Ls, q0, q1, S, CF, lane, t);
                               });
     if (lane == 0) flush_tally(L, t);
   } else {
@@ -674,6 +814,8 @@ static const void* kernel_ptr_p(int gs, bool batch) {
 
 static const void* kernel_ptr(int mode, int gs, int prec, bool batch) {
   if (mode == 1) return gs == 1 ? (const void*)eri_g1_kernel<1, 0, false> : (const void*)eri_g32_kernel<1, 0, false>;
+  if (prec == PREC_PERIODIC)
+    return gs == 1 ? (const void*)eri_g1_kernel<0, 0, false, true> : (const void*)eri_g32_kernel<0, 0, false, true>;
   if (prec == PREC_MIXED64) return kernel_ptr_p<PREC_MIXED64>(gs, batch);
   if (prec == PREC_MIXED32) return kernel_ptr_p<PREC_MIXED32>(gs, batch);
   return kernel_ptr_p<PREC_FP64>(gs, batch);
@@ -704,8 +846,8 @@ cudaError_t eri_prepare() {
     cudaError_t e = cudaFuncSetAttribute(kernel_ptr(1, gs, 0, false), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)mx);
     if (e != cudaSuccess) return e;
-    for (int prec = 0; prec < 3; ++prec)
-      for (int batch = 0; batch < 2; ++batch) {
+    for (int prec = 0; prec < 4; ++prec)
+      for (int batch = 0; batch < (prec == PREC_PERIODIC ? 1 : 2); ++batch) {
         e = cudaFuncSetAttribute(kernel_ptr(0, gs, prec, batch), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
         if (e != cudaSuccess) return e;
       }

@@ -166,6 +166,20 @@ struct SchedVariant {
   int group;   // doubles of the stream regions together, at least the post-contraction scratch
 };
 
+// Lattice images (periodic builds): the library holds the home cell's shells repeated in a
+// box of cells (the image shells, cell-major, the home cell first); every pair of the pair
+// list has one shell in the home cell (list-IJ anchored in the home cell, Sec. 3.1).
+struct PeriodicInfo {
+  const int* shell_cell;            // image shell -> cell index (0 = home cell)
+  const int* shell_bf;              // image shell -> first function in the home-cell numbering
+  const int* cell_xyz;              // cell index -> integer cell coordinates (3 each)
+  const unsigned char* home_first;  // candidate pair -> 1 if its first shell is the home-cell one
+  const int* rmap;                  // density block index of cell R (-1: absent), R in [-rb, rb]^3
+  int rb;
+  const double* P;                  // density blocks P^R, n_R x nbf x nbf
+  int nbf;
+};
+
 // Arguments of one class launch (passed by value).
 struct EriLaunch {
   EriClassInfo ci;
@@ -198,6 +212,9 @@ struct EriLaunch {
   double fp32_tau;              // FP32 iff Q_IJ Q_KL Pmax < fp32_tau, Pmax = max|P_blocks| ...
   const double* pglob;          // ... or, when non-NULL, *pglob = max |P| over the matrix
   double dens_tau;              // > 0: drop quartets with Q_IJ Q_KL max|P_blocks| < dens_tau
+  double dist_tau;              // > 0: drop quartets with Q_IJ Q_KL exp(-kappa rho R^2) < dist_tau
+  const double* dist;           // per sorted pair: most diffuse primitive-pair centre (3), spread,
+                                // smallest exponent sum (5 doubles)
   const double* Qs;             // Schwarz factor of each sorted pair
   // batched launch (n_sys > 0): quartets of all systems' lists for this class, concatenated;
   // seg[s] = first index of system s (seg[n_sys] = total = q_count); batch[s] = that
@@ -205,6 +222,14 @@ struct EriLaunch {
   int n_sys;
   const long long* seg;
   const EriLaunch* batch;
+  // periodic launch: quartets (bra | ket + shift) of the pair list for the cell G; reverse = 0:
+  // the bra pair carries the row function of K^G, 1: the ket pair does (the launch then
+  // evaluates (q | p - G L) for the quartet (p | q + G L) of a lower bra class)
+  PeriodicInfo per;
+  double shift[3];
+  int gcell[3];
+  int reverse;
+  double* KG;                 // K^G, nbf x nbf
 };
 
 

@@ -94,6 +94,48 @@ __global__ void k_pair_flags(long long n_tri, const int* __restrict__ atom, cons
   flag[t] = ok;
 }
 
+// Periodic pair list: candidates t = s * n_img + u, s a home-cell shell (image index s), u
+// any image shell; kept if the shells share an atom (same cell) or their atoms are closer
+// than 2 rcut.
+__global__ void k_pair_flags_rect(long long n, int n_img, const int* __restrict__ atom, const double* __restrict__ xyz,
+                                  double rcut, int* __restrict__ flag) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int s = (int)(t / n_img), u = (int)(t - (long long)s * n_img);
+  const int a = atom[s], b = atom[u];
+  int ok = 1;
+  if (a != b) {
+    const double dx = xyz[3 * a] - xyz[3 * b], dy = xyz[3 * a + 1] - xyz[3 * b + 1], dz = xyz[3 * a + 2] - xyz[3 * b + 2];
+    ok = sqrt(dx * dx + dy * dy + dz * dz) < 2.0 * rcut;
+  }
+  flag[t] = ok;
+}
+
+__global__ void k_pair_setup_rect(int n_cand, const long long* __restrict__ cand_t, int n_img,
+                                  const int* __restrict__ l, const int* __restrict__ nprim,
+                                  const int* __restrict__ atom, const double* __restrict__ xyz, int* __restrict__ sa,
+                                  int* __restrict__ sb, int* __restrict__ pcls, double* __restrict__ AB,
+                                  int* __restrict__ cap, unsigned char* __restrict__ home_first) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cand) return;
+  const long long t = cand_t[c];
+  const int s = (int)(t / n_img), u = (int)(t - (long long)s * n_img);
+  int a = s, b = u;
+  unsigned char hf = 1;
+  if (l[u] > l[s]) {
+    a = u;
+    b = s;
+    hf = 0;
+  }
+  sa[c] = a;
+  sb[c] = b;
+  home_first[c] = hf;
+  const int hi = l[a], lo = l[b];
+  pcls[c] = hi * (hi + 1) / 2 + lo;
+  for (int i = 0; i < 3; ++i) AB[3 * c + i] = xyz[3 * atom[a] + i] - xyz[3 * atom[b] + i];
+  cap[c] = nprim[a] * nprim[b];
+}
+
 // Orientation (l_a >= l_b), pair class, AB and primitive capacity of each candidate.
 __global__ void k_pair_setup(int n_cand, const long long* __restrict__ cand_t, const int* __restrict__ l,
                              const int* __restrict__ nprim, const int* __restrict__ atom,
@@ -157,6 +199,43 @@ __global__ void k_prim_fill(int n_cand, const int* __restrict__ sa, const int* _
   pp_n[c] = n;
 }
 
+// Pair data of the distance-aware test, per candidate pair: the centre of its most diffuse
+// primitive pair (a, b the smallest exponents of the two shells: (a A + b B)/(a + b)), the
+// largest distance of any primitive-pair centre from it (all lie on AB), a + b.
+__global__ void k_pair_dist(int n_cand, const int* __restrict__ sa, const int* __restrict__ sb,
+                            const int* __restrict__ nprim, const int* __restrict__ prim_off_shell,
+                            const int* __restrict__ atom, const double* __restrict__ xyz,
+                            const double* __restrict__ alpha, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cand) return;
+  const int I = sa[c], J = sb[c];
+  const double* A = xyz + 3 * atom[I];
+  const double* B = xyz + 3 * atom[J];
+  double a = alpha[prim_off_shell[I]], b = alpha[prim_off_shell[J]];
+  for (int k = 1; k < nprim[I]; ++k) a = fmin(a, alpha[prim_off_shell[I] + k]);
+  for (int k = 1; k < nprim[J]; ++k) b = fmin(b, alpha[prim_off_shell[J] + k]);
+  double ab = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    out[5 * c + i] = (a * A[i] + b * B[i]) / (a + b);
+    ab += (A[i] - B[i]) * (A[i] - B[i]);
+  }
+  ab = sqrt(ab);
+  double sp = 0.0;
+  for (int k = 0; k < nprim[I]; ++k)
+    for (int kk = 0; kk < nprim[J]; ++kk) {
+      const double x = alpha[prim_off_shell[I] + k], y = alpha[prim_off_shell[J] + kk];
+      sp = fmax(sp, fabs(x / (x + y) - a / (a + b)) * ab);
+    }
+  out[5 * c + 3] = sp;
+  out[5 * c + 4] = a + b;
+}
+
+__global__ void k_gather5(int n, const int* __restrict__ sorted, const double* __restrict__ in, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = 0; k < 5; ++k) out[5 * i + k] = in[5 * sorted[i] + k];
+}
+
 __global__ void k_iota(int n, int* __restrict__ v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = i;
@@ -185,7 +264,7 @@ __global__ void k_gather_q(int n, const int* __restrict__ sorted, const double* 
 // Quartet count of each row (class pair cp = hi(hi+1)/2 + lo, bra position i in bin hi):
 // number of ket positions j in bin lo with Q_i Q_j >= tau (a prefix: bins are sorted by
 // Q descending), and j <= i when hi == lo (each unordered pair of pairs once).
-__global__ void k_count(int n_rows, RowTable rt, const double* __restrict__ Qs, double tau,
+__global__ void k_count(int n_rows, RowTable rt, const double* __restrict__ Qs, double tau, int triangle,
                         long long* __restrict__ row_n) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
@@ -203,7 +282,7 @@ __global__ void k_count(int n_rows, RowTable rt, const double* __restrict__ Qs, 
     if (qi * qk[m] >= tau) a = m + 1; else b = m;
   }
   long long n = a;
-  if (hi == lo && n > i + 1) n = i + 1;
+  if (triangle && hi == lo && n > i + 1) n = i + 1;
   row_n[r] = n;
 }
 
@@ -263,6 +342,21 @@ __global__ void k_symmetrize(int n, int ld, double* __restrict__ K) {
     const int i2 = bj * 32 + r, j2 = bi * 32 + tx;
     const double s2 = tb[r][tx] + ta[tx][r];
     if (bi != bj && i2 < n && j2 < n) K[(size_t)i2 * ld + j2] = s2;
+  }
+}
+
+// B = A^T for n x n row-major blocks (32 x 32 tiles through shared memory)
+__global__ void k_transpose(int n, const double* __restrict__ A, double* __restrict__ B) {
+  __shared__ double t[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = by + r, j = bx + threadIdx.x;
+    if (i < n && j < n) t[r][threadIdx.x] = A[(size_t)i * n + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = bx + r, j = by + threadIdx.x;
+    if (i < n && j < n) B[(size_t)i * n + j] = t[threadIdx.x][r];
   }
 }
 
@@ -462,6 +556,12 @@ cudaError_t launch_normalize(int n_shells, const int* l, const int* nprim, const
   return cudaGetLastError();
 }
 
+cudaError_t launch_transpose(int n, const double* A, double* B, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_transpose<<<dim3(nblk(n, 32), nblk(n, 32)), dim3(32, 8), 0, s>>>(n, A, B);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_boys_table(double* tab, cudaStream_t s) {
   k_boys_table<<<nblk(kBoysRows, 128), 128, 0, s>>>(tab);
   return cudaGetLastError();
@@ -478,6 +578,22 @@ cudaError_t select_flagged(void* tmp, size_t& tmp_bytes, long long n_tri, const 
                            int* d_num, cudaStream_t s) {
   thrust::counting_iterator<long long> it(0);
   return cub::DeviceSelect::Flagged(tmp, tmp_bytes, it, flag, out, d_num, n_tri, s);
+}
+
+cudaError_t launch_pair_flags_rect(long long n, int n_img, const int* atom, const double* xyz, double rcut, int* flag,
+                                   cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_pair_flags_rect<<<nblk(n, 256), 256, 0, s>>>(n, n_img, atom, xyz, rcut, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_setup_rect(int n_cand, const long long* cand_t, int n_img, const int* l, const int* nprim,
+                                   const int* atom, const double* xyz, int* sa, int* sb, int* pcls, double* AB,
+                                   int* cap, unsigned char* home_first, cudaStream_t s) {
+  if (n_cand <= 0) return cudaSuccess;
+  k_pair_setup_rect<<<nblk(n_cand, 256), 256, 0, s>>>(n_cand, cand_t, n_img, l, nprim, atom, xyz, sa, sb, pcls, AB,
+                                                      cap, home_first);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pair_setup(int n_cand, const long long* cand_t, const int* l, const int* nprim,
@@ -503,6 +619,19 @@ cudaError_t launch_prim_fill(int n_cand, const int* sa, const int* sb, const int
   if (n_cand <= 0) return cudaSuccess;
   k_prim_fill<<<nblk(n_cand, 128), 128, 0, s>>>(n_cand, sa, sb, nprim, prim_off_shell, atom, xyz, alpha, w,
                                                  pp_off, prim_tau, pp, pp_n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_dist(int n_cand, const int* sa, const int* sb, const int* nprim, const int* prim_off_shell,
+                             const int* atom, const double* xyz, const double* alpha, double* out, cudaStream_t s) {
+  if (n_cand <= 0) return cudaSuccess;
+  k_pair_dist<<<nblk(n_cand, 128), 128, 0, s>>>(n_cand, sa, sb, nprim, prim_off_shell, atom, xyz, alpha, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather5(int n, const int* sorted, const double* in, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_gather5<<<nblk(n, 128), 128, 0, s>>>(n, sorted, in, out);
   return cudaGetLastError();
 }
 
@@ -546,9 +675,9 @@ cudaError_t launch_gather_q(int n, const int* sorted, const double* Q, double* Q
 }
 
 cudaError_t launch_count(int n_rows, const RowTable& rt, const double* Qs, double tau, long long* row_n,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool triangle) {
   if (n_rows <= 0) return cudaSuccess;
-  k_count<<<nblk(n_rows, 128), 128, 0, s>>>(n_rows, rt, Qs, tau, row_n);
+  k_count<<<nblk(n_rows, 128), 128, 0, s>>>(n_rows, rt, Qs, tau, triangle ? 1 : 0, row_n);
   return cudaGetLastError();
 }
 

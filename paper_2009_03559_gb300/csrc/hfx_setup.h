@@ -35,6 +35,12 @@ cudaError_t launch_pair_flags(long long n_tri, const int* atom, const double* xy
                               cudaStream_t s);
 cudaError_t select_flagged(void* tmp, size_t& tmp_bytes, long long n_tri, const int* flag, long long* out,
                            int* d_num, cudaStream_t s);
+// periodic pair list (home-cell shell x image shell candidates)
+cudaError_t launch_pair_flags_rect(long long n, int n_img, const int* atom, const double* xyz, double rcut, int* flag,
+                                   cudaStream_t s);
+cudaError_t launch_pair_setup_rect(int n_cand, const long long* cand_t, int n_img, const int* l, const int* nprim,
+                                   const int* atom, const double* xyz, int* sa, int* sb, int* pcls, double* AB,
+                                   int* cap, unsigned char* home_first, cudaStream_t s);
 cudaError_t launch_pair_setup(int n_cand, const long long* cand_t, const int* l, const int* nprim,
                               const int* atom, const double* xyz, int* sa, int* sb, int* pcls, double* AB,
                               int* cap, cudaStream_t s);
@@ -44,6 +50,11 @@ cudaError_t scan_ll_inclusive(void* tmp, size_t& tmp_bytes, const long long* in,
 cudaError_t launch_prim_fill(int n_cand, const int* sa, const int* sb, const int* nprim, const int* prim_off_shell,
                              const int* atom, const double* xyz, const double* alpha, const double* w,
                              const int* pp_off, double prim_tau, PrimPair* pp, int* pp_n, cudaStream_t s);
+// distance-aware screening: per candidate pair (centre xyz, spread, smallest exponent sum),
+// and the same gathered into sorted-pair order
+cudaError_t launch_pair_dist(int n_cand, const int* sa, const int* sb, const int* nprim, const int* prim_off_shell,
+                             const int* atom, const double* xyz, const double* alpha, double* out, cudaStream_t s);
+cudaError_t launch_gather5(int n, const int* sorted, const double* in, double* out, cudaStream_t s);
 cudaError_t launch_iota(int n, int* v, cudaStream_t s);
 cudaError_t launch_hist(int n, const int* key, int* counts, cudaStream_t s);
 cudaError_t sort_int_keys(void* tmp, size_t& tmp_bytes, const int* kin, int* kout, const int* vin, int* vout,
@@ -54,8 +65,10 @@ cudaError_t reduce_max(void* tmp, size_t& tmp_bytes, const double* in, double* o
 cudaError_t launch_bin_keys(int n, const double* Q, const double* qmax, double tau, const int* pcls,
                             const int* order, int* binkey, cudaStream_t s);
 cudaError_t launch_gather_q(int n, const int* sorted, const double* Q, double* Qs, cudaStream_t s);
+// triangle: a ket of the bra's own bin only up to the bra (each unordered pair of pairs once);
+// off for periodic builds, whose bra and ket pairs are distinct objects (ket shifted by G)
 cudaError_t launch_count(int n_rows, const RowTable& rt, const double* Qs, double tau, long long* row_n,
-                         cudaStream_t s);
+                         cudaStream_t s, bool triangle = true);
 cudaError_t launch_gather_bounds(const RowTable& rt, const long long* qoff, long long* out, cudaStream_t s);
 cudaError_t launch_finalize(int n, int ld, const double* P, double* K, double* part, int n_part, double* energy,
                             cudaStream_t s);
@@ -65,5 +78,7 @@ cudaError_t launch_pmax(int ns, const int* bf_off, const int* l, const double* P
 cudaError_t launch_batch_prologue(const BatchSys* sys, int n, int n_sm, bool pmax, cudaStream_t s);
 cudaError_t launch_batch_epilogue(const BatchSys* sys, int n, int n_sm, cudaStream_t s);
 cudaError_t fma_peak(double* fp64_tflops, double* fp32_tflops);
+// B = A^T (n x n, row-major, distinct buffers)
+cudaError_t launch_transpose(int n, const double* A, double* B, cudaStream_t s);
 
 }  // namespace hfx

@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
                 ("prim_tau", ctypes.c_double), ("fp32_tau", ctypes.c_double), ("precision", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("skip_zero_p", ctypes.c_int), ("fp32_class_mask", ctypes.c_int),
                 ("fp32_pmax_global", ctypes.c_int), ("reserved", ctypes.c_int * 1),
-                ("density_tau", ctypes.c_double)]
+                ("density_tau", ctypes.c_double), ("dist_tau", ctypes.c_double)]
 
 
 class ServerOptions(ctypes.Structure):
@@ -183,6 +183,13 @@ def load_library(path: str = LIB_PATH):
     L.hfx_measure_fma_peak.restype = ctypes.c_int
     L.hfx_build_K_part.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.hfx_build_K_part.restype = ctypes.c_int
+    L.hfx_init_periodic.argtypes = [ctypes.POINTER(vp), ctypes.c_int, dp, dp, ctypes.c_int, ip, ip, ip, dp, dp,
+                                    ctypes.POINTER(Options), vp]
+    L.hfx_init_periodic.restype = ctypes.c_int
+    L.hfx_periodic_cells.argtypes = [vp, ip, ctypes.c_int]
+    L.hfx_periodic_cells.restype = ctypes.c_int
+    L.hfx_build_K_periodic.argtypes = [vp, ctypes.c_int, ip, vp, ctypes.c_int, ip, vp]
+    L.hfx_build_K_periodic.restype = ctypes.c_int
     i64p = ctypes.POINTER(ctypes.c_int64)
     L.hfx_part_range.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, i64p, i64p]
     L.hfx_part_range.restype = ctypes.c_int
@@ -265,7 +272,7 @@ class HFX:
 
     def __init__(self, system, stream=None, tau=None, rcut=None, omega=None, schedule=HFX_SCHED_DYNAMIC,
                  prim_tau=None, skip_zero_p=True, precision=HFX_FP64, fp32_tau=None, fp32_class_mask=None,
-                 fp32_pmax_global=False, density_tau=0.0):
+                 fp32_pmax_global=False, density_tau=0.0, dist_tau=0.0):
         import torch  # device memory and streams only
         if not torch.cuda.is_available():
             raise RuntimeError("HFX needs a CUDA device; there is no CPU path")
@@ -288,6 +295,7 @@ class HFX:
             o.fp32_class_mask = fp32_class_mask
         o.fp32_pmax_global = 1 if fp32_pmax_global else 0
         o.density_tau = float(density_tau)
+        o.dist_tau = float(dist_tau)
         self.options = o
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         xyz, sa, sl, sn, al, co = system.basis_arrays()
@@ -389,6 +397,61 @@ class HFX:
             self.close()
         except Exception:
             pass
+
+
+class Periodic(HFX):
+    """Lattice sums of the exchange matrix for a crystal (``inputs.PeriodicSystem``): the home
+    cell's basis with its images, list-IJ anchored in the home cell.  ``build_K(P_R, G_list)``
+    takes density blocks {R: n_bf x n_bf array} and returns {G: K^G} (torch CUDA float64)."""
+
+    def __init__(self, ps, stream=None, tau=None, rcut=None, omega=None):
+        import torch  # device memory and streams only
+        if not torch.cuda.is_available():
+            raise RuntimeError("Periodic needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        L = load_library()
+        self.L = L
+        system = ps.cell
+        self.system = system
+        o = default_options()
+        o.omega = system.omega if omega is None else omega
+        o.schwarz_tau = system.tau if tau is None else tau
+        o.rcut_bohr = system.rcut if rcut is None else rcut
+        self.options = o
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        xyz, sa, sl, sn, al, co = system.basis_arrays()
+        lat = np.ascontiguousarray(ps.lattice, dtype=np.float64)
+        self._host = (xyz, sa, sl, sn, al, co, lat)
+        h = ctypes.c_void_p()
+        rc = L.hfx_init_periodic(ctypes.byref(h), int(xyz.shape[0]), _dp(xyz), _dp(lat), int(sl.shape[0]), _ip(sa),
+                                 _ip(sl), _ip(sn), _dp(al), _dp(co), ctypes.byref(o),
+                                 ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise HFXError(rc, L.hfx_last_error(None).decode())
+        self.h = h
+        self.n_bf = system.n_bf
+        self.pairs_built = False
+
+    def cells(self):
+        n = self.L.hfx_periodic_cells(self.h, None, 0)
+        self._check(0 if n >= 0 else n)
+        out = np.zeros(3 * n, dtype=np.int32)
+        self.L.hfx_periodic_cells(self.h, _ip(out), n)
+        return out.reshape(n, 3)
+
+    def build_K(self, P_R, G_list):
+        torch = self.torch
+        n = self.n_bf
+        Rs = sorted(P_R)
+        R_cells = np.ascontiguousarray(np.array(Rs, dtype=np.int32).reshape(-1, 3))
+        P = torch.from_numpy(np.stack([np.asarray(P_R[R], dtype=np.float64) for R in Rs])).cuda()
+        G = np.ascontiguousarray(np.array([tuple(g) for g in G_list], dtype=np.int32).reshape(-1, 3))
+        K = torch.empty((len(G), n, n), dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(self.stream):
+            self._check(self.L.hfx_build_K_periodic(self.h, len(Rs), _ip(R_cells), ctypes.c_void_p(P.data_ptr()),
+                                                    len(G), _ip(G), ctypes.c_void_p(K.data_ptr())))
+        self.stream.synchronize()
+        return {tuple(int(x) for x in g): K[i] for i, g in enumerate(G)}
 
 
 def _ptr_array(values):

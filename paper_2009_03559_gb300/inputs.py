@@ -341,12 +341,13 @@ def periodic_density(ps: PeriodicSystem, r_cells: int, seed: int, truncate_bohr:
 
 
 def periodic_sc(a: float = 6.0, seed: int = 5100, jitter: float = 0.3, tau: float = 1e-10,
-                rcut: float = 3.5, spacing: float | None = None) -> PeriodicSystem:
-    """Simple cubic crystal with one atom per cell (s and p shells, as ``cluster_system``):
-    the smallest periodic case.  ``spacing`` replaces the lattice constant of the images."""
+                rcut: float = 3.5, spacing: float | None = None, shells=(0, 1)) -> PeriodicSystem:
+    """Simple cubic crystal with one atom per cell (by default s and p shells, as
+    ``cluster_system``; ``shells`` lists the angular momenta): the smallest periodic case.
+    ``spacing`` replaces the lattice constant of the images."""
     rng = np.random.default_rng(seed)
     xyz = rng.uniform(-jitter, jitter, (1, 3))
-    sa, sl, sn, al, co = _draw_shells(rng, 1, (0, 1), 3, 0.1, 20.0)
+    sa, sl, sn, al, co = _draw_shells(rng, 1, tuple(shells), 3, 0.1, 20.0)
     cell = System("psc1", xyz, sa, sl, sn, al, co, tau=tau, rcut=rcut, seed=seed, kind="cluster",
                   rng_state=rng.bit_generator.state)
     return PeriodicSystem(cell, np.eye(3) * (a if spacing is None else spacing))
