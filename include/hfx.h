@@ -276,8 +276,8 @@ void hfx_free(hfx_ctx* ctx);
 /* ---------------------------------------------------------------------------
  * Batched K builds: the quartets of several systems (contexts with pair lists) go into
  * one launch per angular class (two under HFX_MIXED: the FP64 and the FP32 share); the
- * class launches are spread over four parallel branches (largest classes first, each to
- * the least loaded branch) so that one class's tail overlaps the next ones; the whole
+ * class launches can be spread over up to four parallel branches (largest classes first,
+ * each to the least loaded branch) so that one class's tail overlaps the next ones; the whole
  * build (zeroing, density block maxima, the class launches, K = A + A^T, E_K per system)
  * is captured once as a CUDA graph and replayed.  The systems' P and K pointers are read from a device table refreshed from
  * host memory before each replay, so new buffers need no new graph.  Precision and
@@ -297,6 +297,8 @@ typedef struct {
                                   previous ones on the whole batch), 0 if it restored them */
   double tune_full_default_ms; /* last hfx_batch_tune: whole batch with the previous choices */
   double tune_full_tuned_ms;   /* ... and with the tuned ones */
+  int32_t branches;            /* parallel branches the class launches are spread over */
+  int32_t reserved_b[1];
 } hfx_batch_stats;
 
 /* Creates a batch over n contexts (all with pair lists, same device).  Runs are ordered
@@ -310,8 +312,9 @@ int hfx_batch_create(hfx_batch** out, hfx_ctx* const* ctxs, int n, void* stream)
  * where the class allows it) and dynamic chunk size (quartets per claim) on one window of
  * the class's quartets, and keeps the fastest; a candidate must beat the current choice by
  * 5% to replace it.  Then it times the whole batch with the previous and with the tuned
- * choices and keeps the tuned ones only if they are faster, so tuning never makes a batch
- * slower than its previous configuration as measured by these runs.  Uses P/K like
+ * choices and keeps the tuned ones only if they are faster (the number of parallel branches,
+ * 1 or 4, is chosen there too), so tuning never makes a batch slower than its previous
+ * configuration as measured by these runs.  Uses P/K like
  * hfx_batch_run (their K contents are overwritten; run hfx_batch_run afterwards).
  * Synchronises. */
 int hfx_batch_tune(hfx_batch* b, const double* const* P_dev, double* const* K_dev, const int* ld);
@@ -324,6 +327,10 @@ int hfx_batch_run(hfx_batch* b, const double* const* P_dev, double* const* K_dev
 /* Launch time the tuner aims at per candidate (default 20 ms): each class's candidates are
  * timed on one window of its quartet list, grown from 16k quartets to about this time. */
 int hfx_batch_set_tune_target(hfx_batch* b, double ms);
+
+/* Parallel branches (streams, graph branches) the class launches are spread over: 1..4
+ * (default 1).  The autotuner also chooses between 1 and 4 on the whole batch. */
+int hfx_batch_set_branches(hfx_batch* b, int n);
 
 /* 1 (default): capture and replay a CUDA graph; 0: plain launches every run. */
 int hfx_batch_set_graph(hfx_batch* b, int enable);
@@ -455,12 +462,20 @@ void hfx_server_free(hfx_server* srv);
  * Scratch: a fixed library-resident device array of 2 * HFX_NOALLOC_MAX_N doubles
  * (256 KiB) on every device that loads the library, kept until process exit.  The
  * first call on a device looks up that array's address (make it before any stream
- * capture).  Calls share the array: calls that overlap on the GPU race, so order them
- * (e.g. one stream).  Each call writes all scratch it reads; nothing needs clearing.
+ * capture) and keeps it for the process: it assumes the device's primary context (the
+ * one the CUDA runtime uses) and no cudaDeviceReset in the process afterwards.  Calls
+ * share the array: calls that overlap on the GPU race, so order them (e.g. one stream).
+ * Each call writes all scratch it reads; nothing needs clearing.
  * Work is queued on `stream` (cudaStream_t, NULL = default).  Errors: HFX_ERR_ARG for
  * NULL pointers, n < 1, n > HFX_NOALLOC_MAX_N or ld < n (message via
  * hfx_last_error(NULL)); HFX_ERR_CUDA if the address lookup or a launch fails. */
 int hfx_energy_noalloc(const double* P_dev, const double* K_dev, int n, int ld, double* E_dev, void* stream);
+
+/* Failure injection for tests (host side: no GPU fault is made): the k-th device
+ * allocation a context makes from now on (k >= 1) fails as if cudaMalloc had returned an
+ * out-of-memory error, so the calling entry point returns HFX_ERR_OOM and releases what it
+ * holds; k = 0 disarms.  Process-wide.  Errors: HFX_ERR_ARG for k < 0. */
+int hfx_debug_fail_alloc(int k);
 
 /* Measures the FP64 and FP32 fused-multiply-add throughput of the current device with
  * a register-resident FMA chain (TFLOP/s, FMA = 2 flops).  Used as the roofline

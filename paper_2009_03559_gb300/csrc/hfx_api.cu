@@ -1,5 +1,6 @@
 // C ABI of the HFX library: context, basis upload, pair-list build, K build.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -20,7 +21,23 @@ static thread_local std::string g_init_err;
 namespace hfx {
 // message for hfx_last_error(NULL) from entry points that have no context
 void set_global_error(const std::string& msg) { g_init_err = msg; }
+
+// allocation-failure injection: the k-th context allocation from the arming call fails
+static std::atomic<int> g_alloc_countdown{0};
+bool alloc_fault_due() {
+  int c = g_alloc_countdown.load();
+  while (c > 0) {
+    if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+  }
+  return false;
+}
 }  // namespace hfx
+
+extern "C" int hfx_debug_fail_alloc(int k) {
+  if (k < 0) return HFX_ERR_ARG;
+  hfx::g_alloc_countdown.store(k);
+  return HFX_OK;
+}
 
 #define CK(call)                                        \
   do {                                                  \

@@ -363,7 +363,7 @@ extern "C" int hfx_batch_create(hfx_batch** out, hfx_ctx* const* ctxs, int n, vo
       return HFX_ERR_CUDA;
     }
   }
-  b->br.n = kBranches;
+  b->br.n = 1;  // measured faster on the 32-system mix; the tuner also tries kBranches
   // per-build scratch: each context's own (a context belongs to one batch build at a time)
   std::vector<double*> pmax(n), pglob(n), energy(n);
   for (int s = 0; s < n; ++s) {
@@ -387,6 +387,13 @@ static int batch_check_args(hfx_batch* b, const double* const* P, double* const*
 extern "C" int hfx_batch_set_tune_target(hfx_batch* b, double ms) {
   if (!b || !(ms > 0.0) || ms > 1e4) return HFX_ERR_ARG;
   b->tune_target_ms = (float)ms;
+  return HFX_OK;
+}
+
+extern "C" int hfx_batch_set_branches(hfx_batch* b, int n) {
+  if (!b || n < 1 || n > kBranches) return HFX_ERR_ARG;
+  b->br.n = n;
+  b->drop_graph();  // a captured graph holds the previous branches
   return HFX_OK;
 }
 
@@ -553,14 +560,28 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
     b->tune_ms[cp] = best * (double)total / (double)win;  // projected to the whole class
     b->tune_window[cp] = win;
   }
-  // the tuned choices replace the incumbent only if the whole batch runs faster with them
+  // the tuned choices replace the incumbent only if the whole batch runs faster with them;
+  // the number of parallel branches is chosen the same way (the incumbent's, or 1 or all)
+  const int br_inc = b->br.n;
+  int br_best = br_inc;
   if (rc == HFX_OK) rc = time_full(&full_new);
+  for (int nb : {1, kBranches}) {
+    if (rc != HFX_OK || nb == br_inc) continue;
+    b->br.n = nb;
+    double ms = 0.0;
+    if ((rc = time_full(&ms)) == HFX_OK && ms < full_new) {
+      full_new = ms;
+      br_best = nb;
+    }
+  }
   if (rc == HFX_OK) {
     b->tune_full_default_ms = full_inc;
     b->tune_full_tuned_ms = full_new;
     b->tune_kept = full_new < full_inc;
+    b->br.n = b->tune_kept ? br_best : br_inc;
     if (!b->tune_kept) restore(incumbent);
   } else {
+    b->br.n = br_inc;
     restore(incumbent);
   }
   cudaEventDestroy(t0);
@@ -586,6 +607,7 @@ extern "C" int hfx_batch_get_stats(hfx_batch* b, hfx_batch_stats* out) {
   out->tune_full_default_ms = b->tune_full_default_ms;
   out->tune_full_tuned_ms = b->tune_full_tuned_ms;
   out->tune_kept = b->tune_kept;
+  out->branches = b->br.n;
   float ms = 0.f;
   if (b->ran && cudaEventElapsedTime(&ms, b->e0, b->e1) == cudaSuccess) out->ms_last = ms;
   return HFX_OK;

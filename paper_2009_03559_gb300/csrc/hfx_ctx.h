@@ -7,6 +7,11 @@
 #include "hfx_internal.cuh"
 #include "hfx_setup.h"
 
+namespace hfx {
+// allocation-failure injection (hfx_debug_fail_alloc): true when this allocation must fail
+bool alloc_fault_due();
+}  // namespace hfx
+
 // device counters per class: primitive quartets evaluated, quartets evaluated, primitive
 // quartets dropped at the Boys step, quartets in FP32, primitive quartets in FP32
 constexpr int kNCnt = 5;
@@ -73,6 +78,7 @@ struct hfx_ctx {
   int alloc(T** p, size_t n, bool pair_scope = false) {
     *p = nullptr;
     if (n == 0) n = 1;
+    if (hfx::alloc_fault_due()) return fail(HFX_ERR_OOM, "cudaMalloc: injected allocation failure");
     cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
     if (e != cudaSuccess) return cuda_fail("cudaMalloc", e);
     (pair_scope ? pair_allocs : allocs).push_back(*p);

@@ -296,7 +296,10 @@ __device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const Sch
 #define HFX_G32_MINB 8
 #endif
 #ifndef HFX_G1B_MINB
-#define HFX_G1B_MINB 4
+#define HFX_G1B_MINB 6
+#endif
+#ifndef HFX_G1F_MINB
+#define HFX_G1F_MINB 4
 #endif
 #ifndef HFX_G32B_MINB
 #define HFX_G32B_MINB 8
@@ -691,7 +694,7 @@ __device__ __forceinline__ void flush_tally(const EriLaunch& L, const Tally& t) 
 }
 
 template <int MODE, int PREC, bool BATCH, bool PER = false>
-__global__ void __launch_bounds__(64, (BATCH || PREC == PREC_MIXED32) ? HFX_G1B_MINB : HFX_G1_MINB)
+__global__ void __launch_bounds__(64, PREC == PREC_MIXED32 ? HFX_G1F_MINB : (BATCH ? HFX_G1B_MINB : HFX_G1_MINB))
     eri_g1_kernel(const EriLaunch L) {
   extern __shared__ double smem[];
   const int st = blockDim.x;

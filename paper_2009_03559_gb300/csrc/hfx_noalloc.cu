@@ -10,7 +10,8 @@
 // The scratch is a file-scope __device__ array.  Host code cannot use its name as a
 // device address, so the first call on each device looks the address up with
 // cudaGetSymbolAddress (with that device current) and caches it; that first call on a
-// device should come before any stream capture.  Every call on a device shares the
+// device should come before any stream capture.  The cache is per device ordinal, for the
+// runtime's primary context: a cudaDeviceReset later in the process would leave it stale.  Every call on a device shares the
 // array: calls whose kernels overlap on the GPU race on it and must be ordered by the
 // caller (e.g. issued on one stream).  The array keeps the previous call's contents;
 // each call writes every row partial it later reads, so nothing has to be cleared.

@@ -102,7 +102,8 @@ class BatchStats(ctypes.Structure):
                 ("group_size_class", ctypes.c_int32 * 21), ("chunk_class", ctypes.c_int32 * 21),
                 ("tune_ms_class", ctypes.c_double * 21), ("tune_window_class", ctypes.c_int64 * 21),
                 ("streams_class", ctypes.c_int32 * 21), ("tune_kept", ctypes.c_int32),
-                ("tune_full_default_ms", ctypes.c_double), ("tune_full_tuned_ms", ctypes.c_double)]
+                ("tune_full_default_ms", ctypes.c_double), ("tune_full_tuned_ms", ctypes.c_double),
+                ("branches", ctypes.c_int32), ("reserved_b", ctypes.c_int32 * 1)]
 
     def as_dict(self):
         return {"n_quartets": int(self.n_quartets), "ms_last": float(self.ms_last),
@@ -112,7 +113,7 @@ class BatchStats(ctypes.Structure):
                 "tune_window_class": [int(x) for x in self.tune_window_class],
                 "streams_class": [int(x) for x in self.streams_class], "tune_kept": int(self.tune_kept),
                 "tune_full_default_ms": float(self.tune_full_default_ms),
-                "tune_full_tuned_ms": float(self.tune_full_tuned_ms)}
+                "tune_full_tuned_ms": float(self.tune_full_tuned_ms), "branches": int(self.branches)}
 
 
 _lib = None
@@ -146,6 +147,8 @@ def load_library(path: str = LIB_PATH):
     L.hfx_get_stats.restype = ctypes.c_int
     L.hfx_set_group_size.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.hfx_set_group_size.restype = ctypes.c_int
+    L.hfx_debug_fail_alloc.argtypes = [ctypes.c_int]
+    L.hfx_debug_fail_alloc.restype = ctypes.c_int
     L.hfx_set_streams.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.hfx_set_streams.restype = ctypes.c_int
     L.hfx_set_timing.argtypes = [vp, ctypes.c_int]
@@ -167,6 +170,8 @@ def load_library(path: str = LIB_PATH):
     L.hfx_batch_tune.restype = ctypes.c_int
     L.hfx_batch_run.argtypes = [vp, pp, pp, ip]
     L.hfx_batch_run.restype = ctypes.c_int
+    L.hfx_batch_set_branches.argtypes = [vp, ctypes.c_int]
+    L.hfx_batch_set_branches.restype = ctypes.c_int
     L.hfx_batch_set_graph.argtypes = [vp, ctypes.c_int]
     L.hfx_batch_set_graph.restype = ctypes.c_int
     L.hfx_batch_set_tune_target.argtypes = [vp, ctypes.c_double]
@@ -485,6 +490,10 @@ class Batch:
     def _check(self, rc):
         if rc != 0:
             raise HFXError(rc, self.L.hfx_last_error(None).decode())
+
+    def set_branches(self, n):
+        """Parallel branches the class launches are spread over (1..4)."""
+        self._check(self.L.hfx_batch_set_branches(self.h, int(n)))
 
     def tune(self, Ps, Ks, target_ms=None):
         if target_ms is not None:

@@ -49,6 +49,32 @@ def test_energy_noalloc_two_calls_match_existing_entry_point():
         h.close()
 
 
+def test_energy_noalloc_strided_rows():
+    """P and K as the left n columns of wider row-major buffers (ld = n + 7), the padding
+    filled with NaN: only the n x n matrices may be read."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_03559_gb300 import hfx
+    L = hfx.load_library()
+    stream = torch.cuda.current_stream()
+    system, P = inputs.config1(8)
+    h, Pd, K, e_ref = _existing_energy(hfx, system, P)
+    n = system.n_bf
+    ld = n + 7
+    Pw = torch.full((n, ld), float("nan"), dtype=torch.float64, device="cuda")
+    Kw = torch.full((n, ld), float("nan"), dtype=torch.float64, device="cuda")
+    Pw[:, :n] = Pd
+    Kw[:, :n] = K
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        rc = L.hfx_energy_noalloc(ctypes.c_void_p(Pw.data_ptr()), ctypes.c_void_p(Kw.data_ptr()), n, ld,
+                                  ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0, L.hfx_last_error(None)
+        torch.cuda.synchronize()
+        assert abs(out.item() - e_ref) <= TOL_E, (out.item(), e_ref)
+    h.close()
+
+
 def test_energy_noalloc_rejects_sizes_beyond_scratch():
     from paper_2009_03559_gb300 import hfx
     L = hfx.load_library()
