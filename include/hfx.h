@@ -482,6 +482,11 @@ int hfx_debug_fail_alloc(int k);
  * denominators for the FP64/FP32 ALU-bound kernels. */
 int hfx_measure_fma_peak(double* fp64_tflops, double* fp32_tflops);
 
+/* Times (ms) the same FP64 FMA-chain kernel with all 32 lanes of every warp active and with
+ * one lane active: equal times show that the FP64 pipe charges each warp instruction in full
+ * whatever the number of active lanes, the property the ERI kernels are laid out around. */
+int hfx_measure_fp64_lane_cost(double* ms_all_lanes, double* ms_one_lane);
+
 #ifdef __cplusplus
 }
 #endif

@@ -565,8 +565,9 @@ extern "C" int hfx_build_K_periodic(hfx_ctx* ctx, int n_R, const int* R_cells, c
   }
   cudaStream_t s = ctx->stream;
   const int nbf = ctx->n_home_bf;
-  int* d_rmap = nullptr;
-  RK(ctx->alloc(&d_rmap, rmap.size(), true));
+  CK(cudaStreamSynchronize(s));  // an earlier build may still read the reused tables
+  RK(ctx->scratch(&ctx->d_rmap, &ctx->rmap_cap, rmap.size()));
+  int* d_rmap = ctx->d_rmap;
   CK(cudaMemcpyAsync(d_rmap, rmap.data(), sizeof(int) * rmap.size(), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(K_G, 0, sizeof(double) * (size_t)n_G * nbf * nbf, s));
   if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], s));
@@ -582,6 +583,13 @@ extern "C" int hfx_build_K_periodic(hfx_ctx* ctx, int n_R, const int* R_cells, c
   L.per.rb = rb;
   L.per.P = P_R;
   L.per.nbf = nbf;
+  // density-block maxima of every P^R (the home shells are the first n_home_shells of the
+  // image basis, so its bf_off / l arrays serve)
+  RK(ctx->scratch(&ctx->d_pmaxR, &ctx->pmaxR_cap, (size_t)n_R * ctx->n_home_shells * ctx->n_home_shells));
+  double* d_pmaxR = ctx->d_pmaxR;
+  CK(launch_pmax_blocks(n_R, ctx->n_home_shells, nbf, ctx->d_bf_off, ctx->d_l, P_R, d_pmaxR, s));
+  L.per.pmax = d_pmaxR;
+  L.per.nsh = ctx->n_home_shells;
   L.schedule = HFX_SCHED_DYNAMIC;
   for (int g = 0; g < n_G; ++g) {
     const int* G = G_cells + 3 * g;
@@ -888,3 +896,13 @@ extern "C" int hfx_measure_fma_peak(double* fp64_tflops, double* fp32_tflops) {
   return HFX_OK;
 }
 
+
+extern "C" int hfx_measure_fp64_lane_cost(double* ms_all_lanes, double* ms_one_lane) {
+  if (!ms_all_lanes || !ms_one_lane) return HFX_ERR_ARG;
+  cudaError_t e = fp64_lane_cost(ms_all_lanes, ms_one_lane);
+  if (e != cudaSuccess) {
+    g_init_err = std::string("lane probe: ") + cudaGetErrorString(e);
+    return HFX_ERR_CUDA;
+  }
+  return HFX_OK;
+}

@@ -61,6 +61,31 @@ struct hfx_ctx {
   std::vector<int> h_cells;              // 3 per cell
   int *d_shell_cell = nullptr, *d_shell_bf = nullptr, *d_cell_xyz = nullptr;
   unsigned char* d_home_first = nullptr;  // per candidate pair (pair scope)
+  // per periodic build, reused while large enough: cell map of the density blocks, their
+  // block maxima
+  int* d_rmap = nullptr;
+  size_t rmap_cap = 0;
+  double* d_pmaxR = nullptr;
+  size_t pmaxR_cap = 0;
+  // a context-lifetime buffer of at least n elements in *p (capacity *cap), reallocated when short
+  template <class T>
+  int scratch(T** p, size_t* cap, size_t n) {
+    if (*p && *cap >= n) return HFX_OK;
+    if (*p) {
+      for (auto it = allocs.begin(); it != allocs.end(); ++it)
+        if (*it == (void*)*p) {
+          allocs.erase(it);
+          break;
+        }
+      cudaFree(*p);
+      bytes -= *cap * sizeof(T);
+      *p = nullptr;
+      *cap = 0;
+    }
+    const int r = alloc(p, n);
+    if (r == HFX_OK) *cap = n;
+    return r;
+  }
   float ms_pairs = 0.f;
   std::vector<void*> allocs;       // owned for the context lifetime
   std::vector<void*> pair_allocs;  // owned until the next build_pairs

@@ -394,6 +394,11 @@ __device__ __forceinline__ bool per_quartet(const EriLaunch& L, int bra, int ket
   }
   const int blk = __ldg(pi.rmap + idx);
   if (blk < 0) return false;
+  // an exactly zero density block P^R_{cd} makes the quartet's contribution exactly zero
+  {
+    const int c = L.reverse ? oys : oxs, d = L.reverse ? oxs : oys;
+    if (__ldg(pi.pmax + ((size_t)blk * pi.nsh + c % pi.nsh) * pi.nsh + d % pi.nsh) == 0.0) return false;
+  }
   q.PR = pi.P + (size_t)blk * pi.nbf * pi.nbf;
   const int phx = hx ? 0 : 1, pox = 1 - phx, phy = hy ? 2 : 3, poy = 5 - phy;
   if (!L.reverse) {

@@ -178,6 +178,8 @@ struct PeriodicInfo {
   int rb;
   const double* P;                  // density blocks P^R, n_R x nbf x nbf
   int nbf;
+  const double* pmax;               // max |P^R| per (R, home shell, home shell): n_R x nsh x nsh
+  int nsh;                          // shells of the home cell
 };
 
 // Arguments of one class launch (passed by value).

@@ -314,6 +314,22 @@ __global__ void k_pmax(int ns, const int* __restrict__ bf_off, const int* __rest
   if (pglob) warp_max_into(m, pglob);  // blockDim is a multiple of 32: whole warps get here
 }
 
+// max |P^R| over each (home shell, home shell) block of every density block: one thread per
+// (R, I, J)
+__global__ void k_pmax_blocks(int n_R, int ns, int nbf, const int* __restrict__ bf_off, const int* __restrict__ l,
+                              const double* __restrict__ P, double* __restrict__ pmax) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n_R * ns * ns) return;
+  const int r = (int)(t / ((long long)ns * ns));
+  const int rem = (int)(t - (long long)r * ns * ns);
+  const int I = rem / ns, J = rem - I * ns;
+  const double* B = P + (size_t)r * nbf * nbf;
+  double m = 0.0;
+  for (int a = 0; a < 2 * l[I] + 1; ++a)
+    for (int b = 0; b < 2 * l[J] + 1; ++b) m = fmax(m, fabs(B[(size_t)(bf_off[I] + a) * nbf + bf_off[J] + b]));
+  pmax[t] = m;
+}
+
 // ---------------------------------------------------------------------------
 // K = A + A^T in place, 32x32 tiles (tile pairs bi <= bj), then E = sum P K with
 // compensated (Neumaier) summation.
@@ -419,14 +435,17 @@ __global__ void k_trace_final(int nb, const double* __restrict__ part, double* _
 // ---------------------------------------------------------------------------
 // FMA-chain throughput probe (register-resident independent chains).
 // ---------------------------------------------------------------------------
+// `active` lanes of every warp run the chains (32: all); the others skip them.
 template <typename T>
-__global__ void k_fma_chain(T* out, int iters, T a, T b) {
+__global__ void k_fma_chain(T* out, int iters, T a, T b, int active) {
   T x[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
-  for (int i = 0; i < iters; ++i) {
+  if ((int)(threadIdx.x & 31) < active) {
+    for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+      for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+    }
   }
   T s = 0;
 #pragma unroll
@@ -559,6 +578,14 @@ cudaError_t launch_normalize(int n_shells, const int* l, const int* nprim, const
 cudaError_t launch_transpose(int n, const double* A, double* B, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   k_transpose<<<dim3(nblk(n, 32), nblk(n, 32)), dim3(32, 8), 0, s>>>(n, A, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pmax_blocks(int n_R, int ns, int nbf, const int* bf_off, const int* l, const double* P,
+                               double* pmax, cudaStream_t s) {
+  const long long n = (long long)n_R * ns * ns;
+  if (n <= 0) return cudaSuccess;
+  k_pmax_blocks<<<nblk(n, 128), 128, 0, s>>>(n_R, ns, nbf, bf_off, l, P, pmax);
   return cudaGetLastError();
 }
 
@@ -737,16 +764,16 @@ cudaError_t fma_peak(double* fp64_tflops, double* fp32_tflops) {
   cudaEventCreate(&e1);
   float ms = 0.f;
   const int it64 = 4096, it32 = 65536;
-  for (int w = 0; w < 2; ++w) k_fma_chain<double><<<blocks, threads>>>(d, it64, 0.999, 1e-4);
+  for (int w = 0; w < 2; ++w) k_fma_chain<double><<<blocks, threads>>>(d, it64, 0.999, 1e-4, 32);
   cudaEventRecord(e0);
-  k_fma_chain<double><<<blocks, threads>>>(d, it64, 0.999, 1e-4);
+  k_fma_chain<double><<<blocks, threads>>>(d, it64, 0.999, 1e-4, 32);
   cudaEventRecord(e1);
   cudaEventSynchronize(e1);
   cudaEventElapsedTime(&ms, e0, e1);
   *fp64_tflops = 2.0 * 8 * (double)it64 * blocks * threads / (ms * 1e-3) / 1e12;
-  for (int w = 0; w < 2; ++w) k_fma_chain<float><<<blocks, threads>>>((float*)d, it32, 0.999f, 1e-4f);
+  for (int w = 0; w < 2; ++w) k_fma_chain<float><<<blocks, threads>>>((float*)d, it32, 0.999f, 1e-4f, 32);
   cudaEventRecord(e0);
-  k_fma_chain<float><<<blocks, threads>>>((float*)d, it32, 0.999f, 1e-4f);
+  k_fma_chain<float><<<blocks, threads>>>((float*)d, it32, 0.999f, 1e-4f, 32);
   cudaEventRecord(e1);
   cudaEventSynchronize(e1);
   cudaEventElapsedTime(&ms, e0, e1);
@@ -758,4 +785,40 @@ cudaError_t fma_peak(double* fp64_tflops, double* fp32_tflops) {
   return e;
 }
 
+}  // namespace hfx
+
+namespace hfx {
+// Time of the FP64 FMA chains with 1 and with 32 active lanes per warp (the same warp
+// instructions; the 1-lane run does 1/32 of the flops): equal times mean the FP64 pipe is
+// charged per warp instruction, not per active lane.
+cudaError_t fp64_lane_cost(double* ms_32, double* ms_1) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  double* d = nullptr;
+  const int blocks = sms * 4, threads = 256, it64 = 4096;
+  e = cudaMalloc(&d, sizeof(double) * blocks * threads);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double* outs[2] = {ms_32, ms_1};
+  const int act[2] = {32, 1};
+  k_fma_chain<double><<<blocks, threads>>>(d, it64, 0.999, 1e-4, 32);
+  for (int r = 0; r < 2; ++r) {
+    float ms = 0.f;
+    cudaEventRecord(e0);
+    k_fma_chain<double><<<blocks, threads>>>(d, it64, 0.999, 1e-4, act[r]);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    *outs[r] = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  e = cudaGetLastError();
+  cudaFree(d);
+  return e;
+}
 }  // namespace hfx

@@ -78,6 +78,10 @@ cudaError_t launch_pmax(int ns, const int* bf_off, const int* l, const double* P
 cudaError_t launch_batch_prologue(const BatchSys* sys, int n, int n_sm, bool pmax, cudaStream_t s);
 cudaError_t launch_batch_epilogue(const BatchSys* sys, int n, int n_sm, cudaStream_t s);
 cudaError_t fma_peak(double* fp64_tflops, double* fp32_tflops);
+cudaError_t fp64_lane_cost(double* ms_32, double* ms_1);
+// periodic: max |P^R| per (R, home shell, home shell) block (bf_off, l of the home shells)
+cudaError_t launch_pmax_blocks(int n_R, int ns, int nbf, const int* bf_off, const int* l, const double* P,
+                               double* pmax, cudaStream_t s);
 // B = A^T (n x n, row-major, distinct buffers)
 cudaError_t launch_transpose(int n, const double* A, double* B, cudaStream_t s);
 

@@ -149,6 +149,8 @@ def load_library(path: str = LIB_PATH):
     L.hfx_set_group_size.restype = ctypes.c_int
     L.hfx_debug_fail_alloc.argtypes = [ctypes.c_int]
     L.hfx_debug_fail_alloc.restype = ctypes.c_int
+    L.hfx_measure_fp64_lane_cost.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.hfx_measure_fp64_lane_cost.restype = ctypes.c_int
     L.hfx_set_streams.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.hfx_set_streams.restype = ctypes.c_int
     L.hfx_set_timing.argtypes = [vp, ctypes.c_int]
@@ -256,6 +258,16 @@ def default_options() -> Options:
     o = Options()
     load_library().hfx_default_options(ctypes.byref(o))
     return o
+
+
+def measure_fp64_lane_cost():
+    """(ms with 32 active lanes, ms with 1 active lane) of the same FP64 FMA-chain kernel."""
+    L = load_library()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = L.hfx_measure_fp64_lane_cost(ctypes.byref(a), ctypes.byref(b))
+    if rc != 0:
+        raise HFXError(rc, L.hfx_last_error(None).decode())
+    return a.value, b.value
 
 
 def measure_fma_peak():
