@@ -351,3 +351,50 @@ def periodic_sc(a: float = 6.0, seed: int = 5100, jitter: float = 0.3, tau: floa
     cell = System("psc1", xyz, sa, sl, sn, al, co, tau=tau, rcut=rcut, seed=seed, kind="cluster",
                   rng_state=rng.bit_generator.state)
     return PeriodicSystem(cell, np.eye(3) * (a if spacing is None else spacing))
+
+
+# ---------------------------------------------------------------------------
+# Synthetic numerical radial functions for the NAO -> GTO fit
+# ---------------------------------------------------------------------------
+@dataclass
+class RadialSet:
+    """Radial functions phi(r_i) on the grid r_i = i h (i = 1..n_r), one row per function."""
+    phi: np.ndarray    # (n_fun, n_r)
+    l: np.ndarray      # (n_fun,) angular momenta
+    h: float
+    r_cut: float
+    zeta: np.ndarray   # the Slater exponents they were drawn with
+    seed: int
+
+
+def confined_slater(l: int, zeta: float, r: np.ndarray, r_cut: float) -> np.ndarray:
+    """r^l exp(-zeta r) (1 - (r / r_cut)^2)^2 inside r_cut, exactly zero beyond: a stand-in for a
+    numerical atomic orbital (strictly confined, value and slope zero at the confining radius)."""
+    x = np.clip(r / r_cut, 0.0, 1.0)
+    f = r ** l * np.exp(-zeta * r) * (1.0 - x * x) ** 2
+    return np.where(r < r_cut, f, 0.0)
+
+
+def nao_set(n_elements: int = 4, seed: int = 6000, r_cut: float = 6.0, n_r: int = 512) -> RadialSet:
+    """DZP-like radial sets (2s, 2p, 1d per element: 5 functions each), Slater exponents
+    log-uniform per element (first zeta in [1.2, 2.4], second zeta 0.45-0.65 of it, d in
+    [0.9, 1.8]), normalised so that sum_i phi_i^2 r_i^2 h = 1."""
+    rng = np.random.default_rng(seed)
+    h = r_cut / n_r
+    r = h * np.arange(1, n_r + 1, dtype=np.float64)
+    rows, ls, zs = [], [], []
+    for _ in range(n_elements):
+        for l in (0, 1):
+            z1 = float(np.exp(rng.uniform(np.log(1.2), np.log(2.4))))
+            z2 = z1 * float(rng.uniform(0.45, 0.65))
+            for z in (z1, z2):
+                rows.append(confined_slater(l, z, r, r_cut))
+                ls.append(l)
+                zs.append(z)
+        z = float(np.exp(rng.uniform(np.log(0.9), np.log(1.8))))
+        rows.append(confined_slater(2, z, r, r_cut))
+        ls.append(2)
+        zs.append(z)
+    phi = np.array(rows)
+    phi /= np.sqrt((phi * phi * (r * r)[None, :]).sum(axis=1) * h)[:, None]
+    return RadialSet(phi, np.array(ls, dtype=np.int32), h, r_cut, np.array(zs), seed)

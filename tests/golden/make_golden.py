@@ -4,11 +4,14 @@ Calls only the CPU oracle (oracle/) and the seeded input generators; nothing her
 touches the CUDA library.  Run from the repository root:
 
     python tests/golden/make_golden.py diamond64    # 64-atom diamond, DZP-like (~ 20 min)
+    python tests/golden/make_golden.py diamond96    # 96-atom piece of the 216-atom diamond (~ 1 h)
     python tests/golden/make_golden.py diamond216   # 216-atom diamond: K blocks only (~ 3 min)
     python tests/golden/make_golden.py batch32      # the 32-system batch: K blocks only (~ 3 min)
 
-Output: tests/golden/oracle_<name>.json.  diamond64: E_K = tr(PK), per-class counts of
-kept canonical quartets, norms of K and a seeded sample of K blocks of the full oracle K.
+Output: tests/golden/oracle_<name>.json.  diamond64 and diamond96: E_K = tr(PK), per-class
+counts of kept canonical quartets, norms of K and a seeded sample of K blocks of the full
+oracle K (diamond96 is the first 96 sites of the 216-atom workload's generator, the largest
+piece of it whose full oracle K a CPU finishes in about an hour).
 diamond216 and batch32 are too large for a full oracle K on a CPU; they store per-class
 counts and K blocks computed one by one (oracle K_block: the sum over all kept quartets
 (I J|K L) P_JL for one shell pair I, K), half of them between shells on nearby atoms,
@@ -29,6 +32,7 @@ from paper_2009_03559_gb300 import inputs  # noqa: E402
 
 CASES = {
     "diamond64": lambda: inputs.config1(64),
+    "diamond96": lambda: inputs.config3(96),
 }
 
 
