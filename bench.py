@@ -25,6 +25,9 @@ Other workloads (one JSON line each, rank 0, one GPU; reports beside the main li
   --workload serve       request stream (Poisson arrivals, systems from a seeded pool)
                          through the continuous-batching server (mixed precision) vs the
                          same stream built one request at a time (plain FP64, FIFO)
+  --workload nao2gto     the NAO -> GTO fit (Algorithm 1) of 20 synthetic confined radial
+                         functions (4 DZP-like element sets), 3 Gaussians each, 512 restarts
+                         per function (population 32, 30 generations, 100 local steps)
 """
 from __future__ import annotations
 
@@ -276,6 +279,120 @@ def run_batch32(args, torch, hfx, inputs):
     }), flush=True)
 
 
+def nao_flops(M, n_r, evals, jpasses, trials):
+    """FP64 flops (FMA = 2) per grid point as the NAO kernels are written, times the passes:
+    genetic fitness = Gaussians by recurrence (2M per pass, two passes), normal equations
+    (M(M+1) + 2M) and residual (2M + 3); Jacobian pass 4M + 3 + 6 M(M+1)/2 + 4M; trial pass
+    4M + 3.  exp() calls (3M per lane and pass) are not counted."""
+    na = M * (M + 1) // 2
+    fit = 2 * M + 2 * na + 2 * M + 2 * M + 2 * M + 3
+    jac = 4 * M + 3 + 6 * na + 4 * M
+    trial = 4 * M + 3
+    return n_r * (evals * fit + jpasses * jac + trials * trial)
+
+
+def run_nao(args, torch, hfx, inputs):
+    """NAO -> GTO fit (paper Sec. "NAO2GTO scheme", Algorithm 1) of a DZP-like radial set."""
+    rs = inputs.nao_set(4)
+    o = hfx.nao_options()
+    n_fun, n_r = rs.phi.shape
+    M, N, P, G = o.n_gauss, o.n_restarts, o.population, o.generations
+    stream = torch.cuda.Stream()
+    F = hfx.NAOFit(rs.phi, rs.l, rs.h, stream=stream)
+    out = F.fit(o)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            F.fit_into(o, out)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    evs = [_evt(torch) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            F.fit_into(o, out)
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    # the genetic kernel alone (the dominant launch), timed the same way
+    ga_evs = [_evt(torch) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ga_evs[i][0].record(stream)
+            F.genetic(o)
+            ga_evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ga_ms = float(np.mean([a.elapsed_time(b) for a, b in ga_evs]))
+    st = out["r_steps"].cpu().numpy()
+    n_rs = n_fun * N
+    evals = n_rs * (P + G * (P - 1) + 1)
+    fl_ga = nao_flops(M, n_r, evals, 0, 0)
+    fl_all = nao_flops(M, n_r, evals, int(st[:, 1].sum()), int(st[:, 0].sum()))
+    fp64_peak, _ = hfx.measure_fma_peak()
+    mean_ms = float(np.mean(ms))
+    # e2e: host radial functions in, best fits out, through the public binding each step
+    e2e_ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):  # the copies back are ordered after the fit
+            Fh = hfx.NAOFit(rs.phi, rs.l, rs.h, stream=stream)
+            res = Fh.fit(o)
+            best = (res["alpha"].cpu(), res["D"].cpu(), res["err"].cpu())
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = rs.phi.nbytes + rs.l.astype(np.int32).nbytes
+    d2h = sum(t.numel() * t.element_size() for t in best)
+    # CPU oracle on a bounded sample of the same restarts
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import nao2gto as ON
+        rng = np.random.default_rng(5)
+        picks = [(int(f), int(it)) for f, it in zip(rng.integers(0, n_fun, 96), rng.integers(0, N, 96))]
+        t0 = time.perf_counter()
+        dev = []
+        for f, it in picks:
+            ref = ON.fit(rs.phi[f], int(rs.l[f]), rs.h, M=M, N=N, P=P, G=G, max_iter=o.max_iter,
+                         alpha_min=o.alpha_min, alpha_max=o.alpha_max, seed=o.seed, fun=f, restarts=[it])
+            q = f * N + it
+            e_gpu = float(out["r_err"][q].item())
+            dev.append(abs(e_gpu - ref["restarts"][0]["err"]) / ref["restarts"][0]["err"])
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(picks) / dt, "unit": "restarts/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(picks)} restarts of the workload drawn uniformly (seeded), {dt:.1f} s",
+               "max_rel_err_diff_gpu_vs_oracle": max(dev)}
+    err = out["err"].cpu().numpy()
+    y2 = [float(((rs.phi[f] / (rs.h * np.arange(1, n_r + 1)) ** rs.l[f]) ** 2).sum()) for f in range(n_fun)]
+    print(json.dumps({
+        "metric": "NAO->GTO fit: Algorithm 1 restarts/s", "workload": "nao2gto",
+        "value": n_rs / (mean_ms * 1e-3), "unit": "restarts/s", "ms_per_step": mean_ms,
+        "p50_ms": float(np.median(ms)), "p99_ms": float(np.percentile(ms, 99)),
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{n_fun} confined Slater-type radial functions (4 elements x 2s 2p 1d), "
+                               f"n_r {n_r} on (0, {rs.r_cut:g}] bohr; M {M}, N {N}, P {P}, G {G}, "
+                               f"max_iter {o.max_iter}, alpha >= {o.alpha_min:g}",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "e2e": {"value": n_rs / (float(np.median(e2e_ms)) * 1e-3), "unit": "restarts/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "alu", "kernel": "nao_genetic_kernel, CUDA events around each launch",
+                     "achieved": fl_ga / (ga_ms * 1e-3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": fl_ga / (ga_ms * 1e-3) / 1e12 / fp64_peak, "traffic": None,
+                     "flops": "per grid point as written (FMA = 2): Gaussian recurrence, normal equations, "
+                              "residual; exp() calls apart", "peak_source": "FP64 FMA-chain probe of this run"},
+        "genetic_ms": ga_ms, "whole_fit_tflops": fl_all / (mean_ms * 1e-3) / 1e12,
+        "fit_rel_err": {"min": float(min(e / y for e, y in zip(err, y2))),
+                        "max": float(max(e / y for e, y in zip(err, y2)))},
+        "local_steps_mean": float(st[:, 0].mean()),
+        "cpu_baseline": cpu,
+        "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"]},
+    }), flush=True)
+
+
 def run_diamond216(args, torch, hfx, inputs):
     """216-atom diamond: plain FP64 build vs mixed precision (FP32 recurrences for quartets
     with Q_IJ Q_KL max|P blocks| < fp32_tau)."""
@@ -443,7 +560,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2000000, help="quartets per oracle step (--impl reference)")
     ap.add_argument("--cpu-sample", type=int, default=5000000,
                     help="quartets of the CPU-oracle baseline on the main line (10-30 s of host work)")
-    ap.add_argument("--workload", default="diamond64", choices=["diamond64", "batch32", "diamond216", "serve", "balance"])
+    ap.add_argument("--workload", default="diamond64", choices=["diamond64", "batch32", "diamond216", "serve", "balance",
+                                                              "nao2gto"])
     ap.add_argument("--requests", type=int, default=32, help="serve: requests of the stream to run")
     ap.add_argument("--rate", type=float, default=0.3, help="serve: offered Poisson rate (requests/s)")
     ap.add_argument("--serve-max-atoms", type=int, default=96, help="serve: largest system of the pool")
@@ -483,7 +601,7 @@ def main():
     if args.workload != "diamond64":
         if rank == 0:
             {"batch32": run_batch32, "diamond216": run_diamond216, "serve": run_serve,
-             "balance": run_balance}[args.workload](
+             "balance": run_balance, "nao2gto": run_nao}[args.workload](
                 args, torch, hfx, inputs)
         if pg:
             pg.destroy_process_group()

@@ -487,6 +487,64 @@ int hfx_measure_fma_peak(double* fp64_tflops, double* fp32_tflops);
  * whatever the number of active lanes, the property the ERI kernels are laid out around. */
 int hfx_measure_fp64_lane_cost(double* ms_all_lanes, double* ms_one_lane);
 
+/* ------------------------------------------------------------------------------------
+ * NAO -> GTO fit (paper Sec. "NAO2GTO scheme" and Algorithm 1).  A numerical radial
+ * function phi (angular momentum l) sampled on the grid r_i = i h, i = 1..n_r, is expanded as
+ *   chi(r) = sum_m D_m r^l exp(-alpha_m r^2),  m = 1..M  (M = n_gauss),
+ * with alpha, D minimising err = sum_i (sum_m D_m exp(-alpha_m r_i^2) - phi(r_i)/r_i^l)^2 under
+ * alpha_m >= alpha_min.  Algorithm 1: n_restarts times, a constrained genetic search gives a
+ * starting point and a constrained local search refines it; the restart with the smallest err
+ * is kept (the first one on ties).  The two searches are the paper's in name only (it does not
+ * spell them out); how they are read here is stated in csrc/hfx_nao.cu.  One warp per restart,
+ * FP64 throughout.  Random draws: SplitMix64 (Steele, Lea and Flood 2014) as a
+ * counter-based generator from `seed`.
+ *
+ * Layouts (all device arrays, row-major, caller-owned; the library allocates nothing):
+ *   phi   n_fun x n_r      l  n_fun ints (0..6)
+ *   per restart q = f * n_restarts + iter:  r_alpha, r_D  (n_fun * n_restarts) x M,
+ *   r_err n_fun * n_restarts, r_steps (n_fun * n_restarts) x 2 ints (trial steps of the
+ *   local search, Jacobian evaluations) or NULL, r_ga_err the err after the genetic step or NULL
+ *   best per function: alpha, D  n_fun x M, err n_fun.  Exponents come out ascending.
+ * Limits: 1 <= n_r <= 1024, 1 <= n_gauss <= 6, 2 <= population <= 64; n_fun = 0 is a no-op
+ * (its pointers may then be NULL).  Work is queued on
+ * `stream` (cudaStream_t, NULL = default).  Errors: HFX_ERR_ARG (NULL pointer, a size or an
+ * option out of range; message via hfx_last_error(NULL)), HFX_ERR_CUDA (launch failed). */
+typedef struct {
+  int n_gauss;             /* M: Gaussians per radial function, 1..6 */
+  int n_restarts;          /* N: iterations of Algorithm 1 per function (the paper: > 500) */
+  int population;          /* P: genetic-search population, 2..64 */
+  int generations;         /* G: genetic-search generations, >= 0 */
+  int max_iter;            /* trial steps of the local search, >= 0 */
+  double alpha_min;        /* lower bound of the exponents (the paper: 0.1) */
+  double alpha_max;        /* upper end of the genetic search's box (> alpha_min) */
+  unsigned long long seed; /* of the counter-based draws */
+} hfx_nao_options;
+
+/* M 3, N 512, P 32, G 30, max_iter 100, alpha_min 0.1, alpha_max 1000, a fixed seed. */
+void hfx_nao_default_options(hfx_nao_options* opt);
+
+/* The whole of Algorithm 1 for n_fun functions: genetic step, local search, selection. */
+int hfx_nao_fit(const double* phi, const int* l, int n_fun, int n_r, double h, const hfx_nao_options* opt,
+                double* alpha, double* D, double* err, double* r_alpha, double* r_D, double* r_err, int* r_steps,
+                double* r_ga_err, void* stream);
+
+/* Its first step alone: per restart the best individual of the genetic search, alpha and the
+ * projected D (the least-squares D for that alpha) with its err. */
+int hfx_nao_genetic(const double* phi, const int* l, int n_fun, int n_r, double h, const hfx_nao_options* opt,
+                    double* alpha, double* D, double* err, void* stream);
+
+/* Its second step alone: the local search started from alpha, D (per restart, updated in
+ * place), err out; steps as r_steps above, or NULL. */
+int hfx_nao_local(const double* phi, const int* l, int n_fun, int n_r, double h, const hfx_nao_options* opt,
+                  double* alpha, double* D, double* err, int* steps, void* stream);
+
+/* The genetic search's fitness for given exponent sets: for set s (function fun_of_set[s],
+ * exponents alpha[s * n_gauss ..]) the least-squares D (ridged normal equations, Cholesky;
+ * D = 0 if the factorisation fails) and err at it.  A set whose function index is outside
+ * 0..n_fun-1 gets NaN for D and err. */
+int hfx_nao_project(const double* phi, const int* l, int n_fun, int n_r, double h, int n_gauss, int n_set,
+                    const int* fun_of_set, const double* alpha, double* D, double* err, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhfx.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["hfx_api.cu", "hfx_eri.cu", "hfx_setup.cu", "hfx_batch.cu", "hfx_noalloc.cu"]
+SOURCES = ["hfx_api.cu", "hfx_eri.cu", "hfx_setup.cu", "hfx_batch.cu", "hfx_noalloc.cu", "hfx_nao.cu"]
 HEADERS = ["hfx_internal.cuh", "eri_engine.cuh", "eri_tables.inc", "hfx_eri.h", "hfx_setup.h", "hfx_ctx.h"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

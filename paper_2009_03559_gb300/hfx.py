@@ -39,6 +39,12 @@ class Options(ctypes.Structure):
                 ("density_tau", ctypes.c_double), ("dist_tau", ctypes.c_double)]
 
 
+class NaoOptions(ctypes.Structure):
+    _fields_ = [("n_gauss", ctypes.c_int), ("n_restarts", ctypes.c_int), ("population", ctypes.c_int),
+                ("generations", ctypes.c_int), ("max_iter", ctypes.c_int), ("alpha_min", ctypes.c_double),
+                ("alpha_max", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+
+
 class ServerOptions(ctypes.Structure):
     _fields_ = [("hbm_budget_gb", ctypes.c_double), ("max_step_quartets", ctypes.c_double),
                 ("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int),
@@ -227,6 +233,19 @@ def load_library(path: str = LIB_PATH):
     L.hfx_server_last_error.restype = ctypes.c_char_p
     L.hfx_server_free.argtypes = [vp]
     L.hfx_server_free.restype = None
+    nop = ctypes.POINTER(NaoOptions)
+    L.hfx_nao_default_options.argtypes = [nop]
+    L.hfx_nao_default_options.restype = None
+    L.hfx_nao_fit.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, nop, vp, vp, vp, vp, vp, vp, vp,
+                              vp, vp]
+    L.hfx_nao_fit.restype = ctypes.c_int
+    L.hfx_nao_genetic.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, nop, vp, vp, vp, vp]
+    L.hfx_nao_genetic.restype = ctypes.c_int
+    L.hfx_nao_local.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, nop, vp, vp, vp, vp, vp]
+    L.hfx_nao_local.restype = ctypes.c_int
+    L.hfx_nao_project.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                  vp, vp, vp, vp, vp]
+    L.hfx_nao_project.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -278,6 +297,98 @@ def measure_fma_peak():
     if rc != 0:
         raise HFXError(rc, L.hfx_last_error(None).decode())
     return a.value, b.value
+
+
+def nao_options(**kw) -> NaoOptions:
+    """hfx_nao_default_options, then the given fields (n_gauss, n_restarts, population,
+    generations, max_iter, alpha_min, alpha_max, seed)."""
+    o = NaoOptions()
+    load_library().hfx_nao_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class NAOFit:
+    """NAO -> GTO fit (paper Sec. "NAO2GTO scheme", Algorithm 1) of radial functions on the
+    grid r_i = i h.  ``phi`` (n_fun x n_r) and ``l`` (n_fun) are uploaded once to torch CUDA
+    tensors; every call runs in the CUDA library on ``stream`` (default: the current stream),
+    so results are read on that stream or after synchronising it."""
+
+    def __init__(self, phi, l, h, stream=None):
+        import torch  # device memory and streams only
+        if not torch.cuda.is_available():
+            raise RuntimeError("the NAO fit needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        self.L = load_library()
+        self.phi = torch.as_tensor(np.ascontiguousarray(phi, dtype=np.float64)).cuda()
+        self.l = torch.as_tensor(np.ascontiguousarray(l, dtype=np.int32)).cuda()
+        self.n_fun, self.n_r = self.phi.shape
+        self.h = float(h)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+
+    def _rc(self, rc):
+        if rc != 0:
+            raise HFXError(rc, self.L.hfx_last_error(None).decode())
+
+    def _z(self, *shape, dtype=None):
+        return self.torch.zeros(*shape, dtype=dtype or self.torch.float64, device=self.phi.device)
+
+    def fit(self, opt: NaoOptions):
+        """Algorithm 1; returns a dict of torch CUDA tensors: best alpha, D (n_fun x M), err
+        (n_fun) and per restart r_alpha, r_D, r_err, r_steps, r_ga_err."""
+        M, N = opt.n_gauss, opt.n_restarts
+        out = {"alpha": self._z(self.n_fun, M), "D": self._z(self.n_fun, M), "err": self._z(self.n_fun),
+               "r_alpha": self._z(self.n_fun * N, M), "r_D": self._z(self.n_fun * N, M),
+               "r_err": self._z(self.n_fun * N), "r_steps": self._z(self.n_fun * N, 2, dtype=self.torch.int32),
+               "r_ga_err": self._z(self.n_fun * N)}
+        self.fit_into(opt, out)
+        return out
+
+    def fit_into(self, opt: NaoOptions, out):
+        """Algorithm 1 into preallocated tensors (the dict `fit` returns)."""
+        p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        self._rc(self.L.hfx_nao_fit(p(self.phi), p(self.l), self.n_fun, self.n_r, self.h, ctypes.byref(opt),
+                                    p(out["alpha"]), p(out["D"]), p(out["err"]), p(out["r_alpha"]), p(out["r_D"]),
+                                    p(out["r_err"]), p(out["r_steps"]), p(out["r_ga_err"]),
+                                    ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def genetic(self, opt: NaoOptions):
+        """The genetic step alone: per restart (alpha, D, err) of its best individual."""
+        M, N = opt.n_gauss, opt.n_restarts
+        a, d, e = self._z(self.n_fun * N, M), self._z(self.n_fun * N, M), self._z(self.n_fun * N)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        self._rc(self.L.hfx_nao_genetic(p(self.phi), p(self.l), self.n_fun, self.n_r, self.h, ctypes.byref(opt),
+                                        p(a), p(d), p(e), ctypes.c_void_p(self.stream.cuda_stream)))
+        return a, d, e
+
+    def local(self, opt: NaoOptions, alpha, D):
+        """The local search alone from per-restart starts (n_fun N x M arrays); returns
+        (alpha, D, err, steps)."""
+        M = opt.n_gauss
+        a = self.torch.as_tensor(np.ascontiguousarray(alpha, dtype=np.float64)).reshape(-1, M).cuda().contiguous()
+        d = self.torch.as_tensor(np.ascontiguousarray(D, dtype=np.float64)).reshape(-1, M).cuda().contiguous()
+        if a.shape[0] != self.n_fun * opt.n_restarts or d.shape != a.shape:
+            raise ValueError("local: one start (M exponents, M coefficients) per restart of every function")
+        e = self._z(a.shape[0])
+        st = self._z(a.shape[0], 2, dtype=self.torch.int32)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        self._rc(self.L.hfx_nao_local(p(self.phi), p(self.l), self.n_fun, self.n_r, self.h, ctypes.byref(opt),
+                                      p(a), p(d), p(e), p(st), ctypes.c_void_p(self.stream.cuda_stream)))
+        return a, d, e, st
+
+    def project(self, M: int, fun_of_set, alpha):
+        """Least-squares D and err for exponent sets (rows of alpha) of the given functions."""
+        fs = self.torch.as_tensor(np.ascontiguousarray(fun_of_set, dtype=np.int32)).cuda()
+        a = self.torch.as_tensor(np.ascontiguousarray(alpha, dtype=np.float64)).reshape(-1, M).cuda().contiguous()
+        n = a.shape[0]
+        d, e = self._z(n, M), self._z(n)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        self._rc(self.L.hfx_nao_project(p(self.phi), p(self.l), self.n_fun, self.n_r, self.h, M, n, p(fs), p(a),
+                                        p(d), p(e), ctypes.c_void_p(self.stream.cuda_stream)))
+        return d, e
 
 
 class HFX:

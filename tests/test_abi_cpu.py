@@ -145,3 +145,28 @@ def test_header_compiles_as_c_and_host_calls_work(lib, tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert "C ABI ok" in r.stdout
+
+
+def test_nao_arguments_checked_on_host(lib):
+    """The NAO-fit entry points reject bad sizes and options before any CUDA call."""
+    from paper_2009_03559_gb300 import hfx
+    o = hfx.nao_options()
+    assert (o.n_gauss, o.n_restarts, o.population, o.generations, o.max_iter) == (3, 512, 32, 30, 100)
+    assert o.alpha_min == 0.1 and o.alpha_max == 1000.0
+    dummy = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
+    args = lambda: (dummy, dummy, 4, 512, 0.01, ctypes.byref(o), dummy, dummy, dummy, dummy, dummy, dummy,  # noqa
+                    None, None, None)
+    for field, bad in (("n_gauss", 0), ("n_gauss", 7), ("population", 1), ("population", 65),
+                       ("n_restarts", 0), ("generations", -1), ("max_iter", -1), ("alpha_min", 0.0),
+                       ("alpha_max", 0.05)):
+        o = hfx.nao_options(**{field: bad})
+        assert lib.hfx_nao_fit(*args()) == -1, field
+    o = hfx.nao_options()
+    assert lib.hfx_nao_fit(dummy, dummy, 4, 1025, 0.01, ctypes.byref(o), dummy, dummy, dummy, dummy, dummy, dummy,
+                           None, None, None) == -1
+    assert lib.hfx_nao_fit(dummy, dummy, 4, 512, 0.0, ctypes.byref(o), dummy, dummy, dummy, dummy, dummy, dummy,
+                           None, None, None) == -1
+    assert lib.hfx_nao_fit(None, dummy, 4, 512, 0.01, ctypes.byref(o), dummy, dummy, dummy, dummy, dummy, dummy,
+                           None, None, None) == -1
+    assert b"nao" in lib.hfx_last_error(None)
+    assert lib.hfx_nao_project(dummy, dummy, 4, 512, 0.01, 3, 5, None, dummy, dummy, dummy, None) == -1

@@ -1,0 +1,170 @@
+"""GPU parity of the NAO -> GTO fit (paper Sec. "NAO2GTO scheme", Algorithm 1) through the C ABI
+against the CPU oracle (oracle/nao2gto.py), on the same synthetic confined radial functions and
+the same counter-based draws.
+
+Tolerances.  The fitness and the residual are sums of n_r squares computed in different orders:
+relative 1e-10.  The coefficients of a least-squares fit are as ill-determined as its normal
+equations, so fits are compared through err and through the fitted curve sum_m D_m e^{-a_m r^2}
+(unique where the minimum is), not coefficient by coefficient.  The genetic and local searches
+branch on comparisons of such sums; both sides take them with the same relative windows
+(1e-12), so the trajectories agree unless a compared value lands within rounding of a window
+edge; Algorithm 1's result (the best of N restarts) is compared at 1e-8."""
+import numpy as np
+import pytest
+
+from oracle import nao2gto as N
+from paper_2009_03559_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fitter():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_03559_gb300 import hfx
+    rs = inputs.nao_set(1)
+    return hfx, rs, hfx.NAOFit(rs.phi, rs.l, rs.h)
+
+
+def curve(alpha, D, r):
+    return N.gaussians(np.asarray(alpha, float), r) @ np.asarray(D, float)
+
+
+def test_projection_matches_oracle(fitter):
+    hfx, rs, F = fitter
+    r = N.grid(rs.phi.shape[1], rs.h)
+    rng = np.random.default_rng(7)
+    for M in range(1, 7):
+        n = 40
+        funs = rng.integers(0, F.n_fun, n)
+        al = np.sort(np.exp(rng.uniform(np.log(0.1), np.log(1000.0), (n, M))), axis=1)
+        D, e = F.project(M, funs, al)
+        D, e = D.cpu().numpy(), e.cpu().numpy()
+        for s in range(n):
+            y = N.targets(rs.phi[funs[s]], int(rs.l[funs[s]]), rs.h)
+            d_o, e_o = N.project(al[s], y, r)
+            assert e[s] == pytest.approx(e_o, rel=1e-10, abs=1e-14 * float(y @ y)), (M, s)
+            assert np.max(np.abs(curve(al[s], D[s], r) - curve(al[s], d_o, r))) <= 1e-6 * np.max(np.abs(y)) + \
+                np.sqrt(max(e_o, 0.0)) * 1e-4
+
+
+def test_genetic_step_matches_oracle(fitter):
+    hfx, rs, F = fitter
+    o = hfx.nao_options(n_gauss=3, n_restarts=6, population=16, generations=4, seed=21)
+    a, d, e = F.genetic(o)
+    a, e = a.cpu().numpy(), e.cpu().numpy()
+    r = N.grid(rs.phi.shape[1], rs.h)
+    for f in range(F.n_fun):
+        y = N.targets(rs.phi[f], int(rs.l[f]), rs.h)
+        for it in range(o.n_restarts):
+            q = f * o.n_restarts + it
+            a_o, d_o, e_o = N.genetic(q, y, r, 3, 16, 4, 0.1, 1000.0, 21)
+            assert np.allclose(a[q], a_o, rtol=1e-12), (f, it)
+            assert e[q] == pytest.approx(e_o, rel=1e-10), (f, it)
+
+
+def test_local_search_matches_oracle(fitter):
+    hfx, rs, F = fitter
+    r = N.grid(rs.phi.shape[1], rs.h)
+    M, Nr = 4, 4
+    o = hfx.nao_options(n_gauss=M, n_restarts=Nr, max_iter=120)
+    rng = np.random.default_rng(3)
+    starts_a = np.sort(np.exp(rng.uniform(np.log(0.15), np.log(200.0), (F.n_fun * Nr, M))), axis=1)
+    starts_d = np.empty_like(starts_a)
+    for q in range(F.n_fun * Nr):
+        f = q // Nr
+        y = N.targets(rs.phi[f], int(rs.l[f]), rs.h)
+        starts_d[q] = N.project(starts_a[q], y, r)[0]
+    a, d, e, st = F.local(o, starts_a, starts_d)
+    a, d, e, st = a.cpu().numpy(), d.cpu().numpy(), e.cpu().numpy(), st.cpu().numpy()
+    same_steps = 0
+    for q in range(F.n_fun * Nr):
+        f = q // Nr
+        y = N.targets(rs.phi[f], int(rs.l[f]), rs.h)
+        a_o, d_o, e_o, it_o = N.local_search(starts_a[q], starts_d[q], y, r, 0.1, 120)
+        assert np.all(a[q] >= 0.1) and np.all(np.diff(a[q]) >= 0)
+        assert e[q] == pytest.approx(N.err(a[q], d[q], y, r), rel=1e-10)
+        assert e[q] == pytest.approx(e_o, rel=1e-8), (q, e[q], e_o, st[q], it_o)
+        assert np.max(np.abs(curve(a[q], d[q], r) - curve(a_o, d_o, r))) <= 1e-5 * np.max(np.abs(y))
+        same_steps += int(st[q, 0] == it_o)
+    assert same_steps >= 0.75 * F.n_fun * Nr
+
+
+def test_algorithm1_matches_oracle(fitter):
+    hfx, rs, F = fitter
+    r = N.grid(rs.phi.shape[1], rs.h)
+    o = hfx.nao_options(n_gauss=3, n_restarts=8, population=24, generations=10, max_iter=100, seed=99)
+    out = {k: v.cpu().numpy() for k, v in F.fit(o).items()}
+    agree = ga_agree = 0
+    for f in range(F.n_fun):
+        y = N.targets(rs.phi[f], int(rs.l[f]), rs.h)
+        ref = N.fit(rs.phi[f], int(rs.l[f]), rs.h, M=3, N=8, P=24, G=10, max_iter=100, seed=99, fun=f)
+        assert out["err"][f] == pytest.approx(ref["best"]["err"], rel=1e-8)
+        assert np.max(np.abs(curve(out["alpha"][f], out["D"][f], r) - curve(ref["best"]["alpha"],
+                                                                              ref["best"]["D"], r))) \
+            <= 1e-5 * np.max(np.abs(y))
+        assert out["err"][f] == min(out["r_err"][f * 8:(f + 1) * 8])
+        for it, p in enumerate(ref["restarts"]):
+            q = f * 8 + it
+            ga_o = N.err(p["ga_alpha"], p["ga_D"], y, r)
+            ga_agree += int(abs(out["r_ga_err"][q] - ga_o) <= 1e-8 * ga_o)
+            agree += int(abs(out["r_err"][q] - p["err"]) <= 1e-8 * p["err"])
+            assert np.all(out["r_alpha"][q] >= 0.1)
+    assert agree >= 0.9 * F.n_fun * 8
+    assert ga_agree >= 0.9 * F.n_fun * 8
+
+
+def test_ragged_grid_and_active_bound(fitter):
+    """n_r not a multiple of the warp width; a target that pins the exponent on alpha_min."""
+    hfx, _, _ = fitter
+    n_r, h = 300, 6.0 / 300
+    r = N.grid(n_r, h)
+    phi = np.stack([np.exp(-0.03 * r * r), r * np.exp(-1.3 * r) * (1 - (r / 6.0) ** 2) ** 2])
+    F = hfx.NAOFit(phi, [0, 1], h)
+    o = hfx.nao_options(n_gauss=1, n_restarts=3, population=8, generations=5, max_iter=80, seed=4)
+    out = {k: v.cpu().numpy() for k, v in F.fit(o).items()}
+    assert out["alpha"][0, 0] == 0.1
+    for f in range(2):
+        ref = N.fit(phi[f], [0, 1][f], h, M=1, N=3, P=8, G=5, max_iter=80, seed=4, fun=f)
+        assert out["err"][f] == pytest.approx(ref["best"]["err"], rel=1e-8)
+
+
+def test_exact_recovery(fitter):
+    hfx, _, _ = fitter
+    n_r, h = 512, 6.0 / 512
+    r = N.grid(n_r, h)
+    a_true, d_true = np.array([0.3, 1.7, 9.0]), np.array([0.5, -0.8, 1.2])
+    y = N.gaussians(a_true, r) @ d_true
+    F = hfx.NAOFit(y[None, :], [0], h)
+    out = {k: v.cpu().numpy() for k, v in F.fit(hfx.nao_options(n_restarts=4, generations=20, max_iter=200)).items()}
+    assert out["err"][0] <= 1e-22 * float(y @ y)
+    assert np.allclose(out["alpha"][0], a_true, rtol=1e-6)
+
+
+def test_empty_and_default_workload_sampled(fitter):
+    """n_fun = 0 is a no-op; the benchmark's configuration (20 functions, 512 restarts,
+    default options), checked on sampled restarts that the oracle recomputes one by one."""
+    hfx, _, _ = fitter
+    import torch
+    rs = inputs.nao_set(4)
+    F0 = hfx.NAOFit(np.zeros((0, 64)), np.zeros(0, np.int32), 0.1)
+    F0.fit(hfx.nao_options(n_restarts=2))
+    F = hfx.NAOFit(rs.phi, rs.l, rs.h)
+    o = hfx.nao_options()
+    out = {k: v.cpu().numpy() for k, v in F.fit(o).items()}
+    torch.cuda.synchronize()
+    r = N.grid(rs.phi.shape[1], rs.h)
+    rng = np.random.default_rng(17)
+    for f, it in zip(rng.integers(0, 20, 4), rng.integers(0, 512, 4)):
+        y = N.targets(rs.phi[f], int(rs.l[f]), rs.h)
+        ref = N.fit(rs.phi[f], int(rs.l[f]), rs.h, M=o.n_gauss, N=512, P=o.population, G=o.generations,
+                    max_iter=o.max_iter, alpha_min=o.alpha_min, alpha_max=o.alpha_max, seed=o.seed, fun=int(f),
+                    restarts=[int(it)])
+        q = int(f) * 512 + int(it)
+        assert out["r_err"][q] == pytest.approx(ref["restarts"][0]["err"], rel=1e-6)
+    for f in range(20):
+        assert out["err"][f] == out["r_err"][f * 512:(f + 1) * 512].min()
+        y = N.targets(rs.phi[f], int(rs.l[f]), rs.h)
+        assert out["err"][f] == pytest.approx(N.err(out["alpha"][f], out["D"][f], y, r), rel=1e-10)
