@@ -55,7 +55,8 @@ def class_mask(hfx, name):
 
 def workload_desc(s, mixed=False, fp32_classes="default"):
     prec = ("mixed precision (FP32 recurrences where Q*Q*max|P| < 1e-6, "
-            f"{MASK_DESC[fp32_classes]}; FP64 Boys step, HRR, spherical step and K)" if mixed else "plain FP64")
+            f"{MASK_DESC[fp32_classes]}; FP32 Boys step where the incomplete-gamma difference is safe, else "
+            f"FP64; FP64 HRR, spherical step and K)" if mixed else "plain FP64")
     return (f"diamond-{s.n_atoms} DZP-like: {s.n_atoms} atoms (a=10.26 bohr cells), {s.n_shells} shells "
             f"s,s,p,p,d, {s.n_bf} spherical functions, 3 primitives/shell, omega=0.11, r_c=6 bohr, "
             f"tau=1e-8, P truncated beyond 10 bohr; {prec}")

@@ -75,11 +75,15 @@ typedef struct {
   double schwarz_tau;  /* Schwarz threshold tau (>= 0) */
   double rcut_bohr;    /* orbital cutoff radius r_c; <= 0 disables the pair-distance screen */
   double prim_tau;     /* primitive pairs with |prefactor| below this are dropped (default 1e-22) */
-  double fp32_tau;     /* HFX_MIXED: a quartet's primitive recurrences (VRR) and their contraction
-                          run in FP32 iff Q_IJ Q_KL Pmax < fp32_tau (default 1e-6), Pmax as set
-                          by fp32_pmax_global; the Boys step, HRR, spherical step and all K
-                          accumulation stay FP64.  The warp kernel runs FP32 quartets packed,
-                          two primitive quartets per float2 slot (FFMA2) */
+  double fp32_tau;     /* HFX_MIXED: a quartet's primitive set-up, recurrences (VRR) and their
+                          contraction run in FP32 iff Q_IJ Q_KL Pmax < fp32_tau (default 1e-6),
+                          Pmax as set by fp32_pmax_global; HRR, spherical step and all K
+                          accumulation stay FP64.  The FP32 Boys step is the difference of two
+                          upper incomplete gamma functions (erfc and an upward recursion of
+                          positive terms); a primitive quartet where the subtracted one exceeds
+                          1/64 of the other (small T (1 - kappa)) takes the FP64 Boys step.  FP32
+                          quartets run on whole warps, two primitive quartets per float2 slot
+                          (FFMA2) */
   int precision;       /* HFX_FP64 (default) or HFX_MIXED */
   int schedule;        /* HFX_SCHED_DYNAMIC (default), HFX_SCHED_QUARTET or HFX_SCHED_PAIR */
   int skip_zero_p;     /* 1 (default): skip quartets whose four density blocks P_bd, P_bc,

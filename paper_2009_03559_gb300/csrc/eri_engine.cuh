@@ -176,6 +176,131 @@ __device__ __forceinline__ bool prim_setup(const PrimPair& b, const PrimPair& k,
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 set-up (FP32 passes of the mixed-precision build).  With a = m + 1/2,
+//   F_m(T) - kappa^a F_m(kappa T) = 1/2 T^{-a} (Gamma(a, kappa T) - Gamma(a, T)),
+// because F_m(x) = 1/2 x^{-a} gamma(a, x) and gamma(a, x) = Gamma(a) - Gamma(a, x).  So with
+// A_m = 1/2 T^{-a} Gamma(a, kappa T) and B_m = 1/2 T^{-a} Gamma(a, T), from Gamma(1/2, x) =
+// sqrt(pi) erfc(sqrt x) and Gamma(a + 1, x) = a Gamma(a, x) + x^a e^{-x}:
+//   A_0 = 1/2 sqrt(pi/T) erfc(sqrt(kappa T)),  A_{m+1} = ((m + 1/2) A_m + 1/2 kappa^{m+1/2} e^{-kappa T}) / T,
+//   B_0 = 1/2 sqrt(pi/T) erfc(sqrt(T)),        B_{m+1} = ((m + 1/2) B_m + 1/2 e^{-T}) / T.
+// Every term is positive, so this upward recursion keeps FP32's relative accuracy at any T; the
+// one subtraction, G_m = pref (A_m - B_m), loses at most a factor 1 / (1 - B_m / A_m).  Where
+// B_m > A_m / 64 for some m (T (1 - kappa) small: close or diffuse pairs) the primitive quartet
+// takes the FP64 set-up instead.  P - Q is formed in FP64 (3 instructions), so that T keeps
+// FP32's relative accuracy for centres far from the origin; nothing else runs on the FP64 pipe.
+// ---------------------------------------------------------------------------
+struct PrimScalarsF {
+  float RP, RQ, inv_s, PQ[3];
+};
+
+enum { F32_SKIP = 0, F32_OK = 1, F32_FP64 = 2 };
+
+__device__ __forceinline__ int prim_core_f32(const PrimPair& b, const PrimPair& k, int Lt, float omega_f, float* G,
+                                             PrimScalarsF& ps) {
+  const float p = b.pf, q = k.pf;
+  const float y = rsqrtf(p + q);  // 1/sqrt(p+q)
+  const float inv_s = y * y;
+  ps.inv_s = inv_s;
+  ps.RP = q * inv_s;
+  ps.RQ = p * inv_s;
+  const float rho = p * ps.RP;
+  ps.PQ[0] = to_f32(b.P[0] - k.P[0]);
+  ps.PQ[1] = to_f32(b.P[1] - k.P[1]);
+  ps.PQ[2] = to_f32(b.P[2] - k.P[2]);
+  const float T = rho * fmaf(ps.PQ[0], ps.PQ[0], fmaf(ps.PQ[1], ps.PQ[1], ps.PQ[2] * ps.PQ[2]));
+  const float sk = omega_f * rsqrtf(fmaf(omega_f, omega_f, rho));  // sqrt(kappa)
+  const float kap = sk * sk;
+  const float kT = kap * T;
+  if (kT >= 60.0f) return F32_SKIP;  // as the FP64 set-up: G_m < e^{-60}
+  const float pref = to_f32(b.C) * to_f32(k.C) * y;
+  const float yT = rsqrtf(T);
+  const float invT = yT * yT;
+  const float c0 = 0.886226925f * yT;  // sqrt(pi) / 2 / sqrt(T)
+  float A = c0 * erfcf(sqrtf(kT));
+  float B = c0 * erfcf(sqrtf(T));
+  const float hk = 0.5f * expf(-kT), h1 = 0.5f * expf(-T);
+  // accepted only with B_m <= A_m / 64 and A_m finite at every order (on this path A_m stays far
+  // below 1: T (1 - kappa) is not small); T near 0 overflows the recursion and is declined
+  bool ok = (B <= A * (1.0f / 64.0f)) && (A <= 1e30f);
+  G[0] = pref * (A - B);
+  float kp = sk;  // kappa^{m+1/2}
+#pragma unroll
+  for (int m = 0; m < kMaxLt; ++m) {
+    if (m < Lt) {
+      const float a = (float)m + 0.5f;
+      A = fmaf(a, A, kp * hk) * invT;
+      B = fmaf(a, B, h1) * invT;
+      kp *= kap;
+      ok = ok && (B <= A * (1.0f / 64.0f)) && (A <= 1e30f);
+      G[m + 1] = pref * (A - B);
+    }
+  }
+  return ok ? F32_OK : F32_FP64;
+}
+
+// Register coefficients from the FP32 set-up (one quartet per thread).
+__device__ __forceinline__ int prim_setup_f32(const PrimPair& b, const PrimPair& k, int E, int F, int Lt,
+                                              float omega_f, CoefRgT<float>& c, float* G) {
+  PrimScalarsF ps;
+  const int st = prim_core_f32(b, k, Lt, omega_f, G, ps);
+  if (st != F32_OK) return st;
+  if (E > 0) {
+    c.PA[0] = b.PAf[0]; c.PA[1] = b.PAf[1]; c.PA[2] = b.PAf[2];
+    c.WP[0] = -ps.RP * ps.PQ[0]; c.WP[1] = -ps.RP * ps.PQ[1]; c.WP[2] = -ps.RP * ps.PQ[2];
+    c.ca1 = b.inv2pf; c.ca2 = 2.0f * b.inv2pf; c.ca3 = 3.0f * b.inv2pf;
+    c.RP = ps.RP;
+  }
+  if (F > 0) {
+    c.QC[0] = k.PAf[0]; c.QC[1] = k.PAf[1]; c.QC[2] = k.PAf[2];
+    c.WQ[0] = ps.RQ * ps.PQ[0]; c.WQ[1] = ps.RQ * ps.PQ[1]; c.WQ[2] = ps.RQ * ps.PQ[2];
+    c.ck1 = k.inv2pf; c.ck2 = 2.0f * k.inv2pf; c.ck3 = 3.0f * k.inv2pf;
+    c.RQ = ps.RQ;
+    c.cb1 = 0.5f * ps.inv_s; c.cb2 = ps.inv_s; c.cb3 = 1.5f * ps.inv_s; c.cb4 = 2.0f * ps.inv_s;
+  }
+  return F32_OK;
+}
+
+// A coefficient set (layout of write_set) from the FP32 set-up values.
+template <int CS = 1>
+__device__ __forceinline__ void write_set_f32(const PrimPair& b, const PrimPair& k, int E, int F, int Lt,
+                                              const float* G, const PrimScalarsF& ps, float* cf) {
+#pragma unroll
+  for (int m = 0; m <= kMaxLt; ++m)
+    if (m <= Lt) cf[(HFX_CF_G + m) * CS] = G[m];
+  cf[(HFX_CF_ONE) * CS] = 1.0f;
+  cf[(HFX_CF_ZERO) * CS] = 0.0f;
+  cf[(HFX_CF_CA) * CS] = 0.0f;
+  cf[(HFX_CF_CK) * CS] = 0.0f;
+  cf[(HFX_CF_CB) * CS] = 0.0f;
+  if (E > 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      cf[(HFX_CF_PA + i) * CS] = b.PAf[i];
+      cf[(HFX_CF_WP + i) * CS] = -ps.RP * ps.PQ[i];
+    }
+    cf[(HFX_CF_CA + 1) * CS] = b.inv2pf;
+    cf[(HFX_CF_CA + 2) * CS] = 2.0f * b.inv2pf;
+    cf[(HFX_CF_CA + 3) * CS] = 3.0f * b.inv2pf;
+    cf[HFX_CF_RP * CS] = -ps.RP;
+  }
+  if (F > 0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      cf[(HFX_CF_QC + i) * CS] = k.PAf[i];
+      cf[(HFX_CF_WQ + i) * CS] = ps.RQ * ps.PQ[i];
+    }
+    cf[(HFX_CF_CK + 1) * CS] = k.inv2pf;
+    cf[(HFX_CF_CK + 2) * CS] = 2.0f * k.inv2pf;
+    cf[(HFX_CF_CK + 3) * CS] = 3.0f * k.inv2pf;
+    cf[HFX_CF_RQ * CS] = -ps.RQ;
+    cf[(HFX_CF_CB + 1) * CS] = 0.5f * ps.inv_s;
+    cf[(HFX_CF_CB + 2) * CS] = ps.inv_s;
+    cf[(HFX_CF_CB + 3) * CS] = 1.5f * ps.inv_s;
+    cf[(HFX_CF_CB + 4) * CS] = 2.0f * ps.inv_s;
+  }
+}
+
 // A coefficient set in group scratch (warp kernel) from the set-up values, in the precision
 // R of the recurrences: every set-up step runs in FP64; an FP32 set is the rounded FP64 one.
 template <typename R>

@@ -733,8 +733,12 @@ static int build_K_impl(hfx_ctx* ctx, const double* P, double* K, int ld, int pa
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[2 + 2 * cp], s));
     for (int pass = 0; pass < (L.fp32_ok ? 2 : 1); ++pass) {
       const int prec = L.fp32_ok ? 1 + pass : 0;
+      // the FP32 pass runs on whole warps in every class (packed FP32 recurrences after an
+      // FP32 set-up), unless the caller fixed the class's group size
+      const int gsp = (prec == 2 && !ctx->gs_override[cp]) ? 32 : gs;
+      L.chunk = gsp == 1 ? 256 : 8;
       L.work = ctx->d_work + cp + 21 * pass;
-      CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items, gs, prec, false, streams), s, gs, prec, false, streams));
+      CK(eri_launch(L, cp, 0, grid_for(ctx, cp, 0, items, gsp, prec, false, streams), s, gsp, prec, false, streams));
     }
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[3 + 2 * cp], s));
     ctx->class_launched[cp] = true;

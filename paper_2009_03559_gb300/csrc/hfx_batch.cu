@@ -173,6 +173,12 @@ void bw_set_buffers(BatchWork& w, const double* const* P, double* const* K, cons
 
 // launch record of class cp, precision pass `pass` (0, or 0/1 for a mixed class's FP64/FP32
 // passes: each has its own work counter)
+int bw_prec(const BatchWork& w, int cp, int pass) { return w.fp32_class[cp] ? 1 + pass : 0; }
+
+// lanes per quartet of a pass: the class's choice, except the FP32 pass, which runs on whole
+// warps in every class (packed FP32 recurrences after an FP32 set-up)
+int bw_gs(const BatchWork& w, int cp, int prec) { return prec == 2 ? 32 : w.gs[cp]; }
+
 EriLaunch bw_class_launch(const BatchWork& w, int cp, int pass = 0) {
   EriLaunch L;
   std::memset(&L, 0, sizeof(L));
@@ -180,19 +186,18 @@ EriLaunch bw_class_launch(const BatchWork& w, int cp, int pass = 0) {
   L.schedule = HFX_SCHED_DYNAMIC;
   L.q_count = w.total[cp];
   L.work = w.d_work + cp + 21 * pass;
-  L.chunk = w.chunk[cp];
+  L.chunk = bw_gs(w, cp, bw_prec(w, cp, pass)) == w.gs[cp] ? w.chunk[cp] : 8;
   L.n_sys = w.n;
   L.seg = w.d_seg + (size_t)cp * (w.cap + 1);
   L.batch = w.d_launch + (size_t)cp * w.cap;
   return L;
 }
 
-int bw_prec(const BatchWork& w, int cp, int pass) { return w.fp32_class[cp] ? 1 + pass : 0; }
-
 int bw_grid(const BatchWork& w, int cp, long long items, int prec) {
-  const long long groups_per_block = eri_groups_per_block(w.gs[cp]);
+  const int gs = bw_gs(w, cp, prec);
+  const long long groups_per_block = eri_groups_per_block(gs);
   const long long need = (items + groups_per_block - 1) / groups_per_block;
-  const long long cap = (long long)eri_blocks_per_sm(cp, 0, w.gs[cp], prec, true, w.streams[cp]) * w.n_sm;
+  const long long cap = (long long)eri_blocks_per_sm(cp, 0, gs, prec, true, w.streams[cp]) * w.n_sm;
   return (int)std::max(1LL, std::min(need, cap));
 }
 
@@ -252,9 +257,8 @@ cudaError_t bw_enqueue(const BatchWork& w, cudaStream_t s, const Branches* br = 
     for (int pass = 0; pass < (w.fp32_class[cp] ? 2 : 1); ++pass) {
       const EriLaunch L = bw_class_launch(w, cp, pass);
       const int prec = bw_prec(w, cp, pass);
-      if ((e = eri_launch(L, cp, 0, bw_grid(w, cp, w.total[cp], prec), bs, w.gs[cp], prec, true, w.streams[cp])) !=
-          cudaSuccess)
-        return e;
+      e = eri_launch(L, cp, 0, bw_grid(w, cp, w.total[cp], prec), bs, bw_gs(w, cp, prec), prec, true, w.streams[cp]);
+      if (e != cudaSuccess) return e;
     }
   }
   if (nb > 1) {
@@ -488,7 +492,7 @@ extern "C" int hfx_batch_tune(hfx_batch* b, const double* const* P, double* cons
         EriLaunch L = bw_class_launch(w, cp, pass);
         L.q_count = w1;
         const int prec = bw_prec(w, cp, pass);
-        CKB(eri_launch(L, cp, 0, bw_grid(w, cp, w1 - w0, prec), s, w.gs[cp], prec, true, w.streams[cp]));
+        CKB(eri_launch(L, cp, 0, bw_grid(w, cp, w1 - w0, prec), s, bw_gs(w, cp, prec), prec, true, w.streams[cp]));
       }
       CKB(cudaEventRecord(t1, s));
       CKB(cudaEventSynchronize(t1));

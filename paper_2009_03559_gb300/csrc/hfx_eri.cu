@@ -38,9 +38,79 @@ __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaun
   // one flat loop over the primitive quartets: lanes whose quartets have the same count
   // (the queue groups them so) run the same number of iterations
   const int npq = nb * nk;
-  for (int t = 0; t < npq; ++t) {
-    const int ib = t / nk, ik = t - ib * nk;
-    {
+  if constexpr (sizeof(R) == 4) {
+    static_assert(!PER, "the periodic build runs in FP64");
+    // vertical recurrences and contraction on FP32 slots for one primitive quartet
+    auto vrr = [&](const CoefRgT<float>& cf, const float* Gf) {
+      for (int m = 0; m <= ci.Lt; ++m) V[m * sts] = Gf[m];
+      for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
+        const int off = ci.lv_off[lv], n = ci.lv_n[lv];
+        for (int o = 0; o < n; ++o) vrr_bra<true>(ld_op(kVrrOps, off + o), V, S, sts, cf);
+      }
+      for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
+        const int off = ci.lv_off[lv], n = ci.lv_n[lv];
+        for (int o = 0; o < n; ++o) vrr_ket<true>(ld_op(kVrrOps, off + o), V, S, sts, cf);
+      }
+      for (int a = 0; a < ci.n_accl; ++a) {
+        const uint32_t w = __ldg(kAccSrc + ci.acc_off + a);
+        S[(w & 0xFFFF) * sts] += V[(w >> 16) * sts];
+      }
+    };
+    // the FP64 set-up of one primitive quartet, rounded to FP32 (false: negligible)
+    auto setup64 = [&](int t, CoefRgT<float>& cf, float* Gf) {
+      const int ib = t / nk, ik = t - ib * nk;
+      CoefRg c;
+      double Gm[kMaxLt + 1];
+      if (!prim_setup(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, omega, omega2, boys, c, Gm)) return false;
+      cf = coef_f32(c, ci.E, ci.F);
+      for (int m = 0; m <= ci.Lt; ++m) Gf[m] = to_f32(Gm[m]);
+      return true;
+    };
+    // FP32 set-up first; the primitive quartets it declines (bit t - c0 of pend) take the FP64
+    // set-up at the end of their chunk of 96, so that a lane's FP64 set-ups run together with
+    // the other lanes' instead of once per iteration in which any lane needs one
+    const float omega_f = to_f32(omega);
+    for (int c0 = 0; c0 < npq; c0 += 96) {
+      const int c1 = min(npq, c0 + 96);
+      unsigned pend0 = 0, pend1 = 0, pend2 = 0;
+      for (int t = c0; t < c1; ++t) {
+        const int ib = t / nk, ik = t - ib * nk;
+        CoefRgT<float> cf;
+        float Gf[kMaxLt + 1];
+        const int stt = prim_setup_f32(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, omega_f, cf, Gf);
+        if (stt == F32_SKIP) continue;
+        if (stt == F32_FP64) {
+          const int u = t - c0;
+          if (u < 32) pend0 |= 1u << u;
+          else if (u < 64) pend1 |= 1u << (u - 32);
+          else pend2 |= 1u << (u - 64);
+          continue;
+        }
+        ++any;
+        vrr(cf, Gf);
+      }
+      while (pend0 | pend1 | pend2) {
+        int t;
+        if (pend0) {
+          t = c0 + __ffs(pend0) - 1;
+          pend0 &= pend0 - 1;
+        } else if (pend1) {
+          t = c0 + 32 + __ffs(pend1) - 1;
+          pend1 &= pend1 - 1;
+        } else {
+          t = c0 + 64 + __ffs(pend2) - 1;
+          pend2 &= pend2 - 1;
+        }
+        CoefRgT<float> cf;
+        float Gf[kMaxLt + 1];
+        if (!setup64(t, cf, Gf)) continue;
+        ++any;
+        vrr(cf, Gf);
+      }
+    }
+  } else {
+    for (int t = 0; t < npq; ++t) {
+      const int ib = t / nk, ik = t - ib * nk;
       const PrimPair b = pb[ib];
       PrimPair k = pk[ik];
       if constexpr (PER) {  // the ket pair's image in cell G (its centre moves, P - C does not)
@@ -52,27 +122,14 @@ __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaun
       double Gm[kMaxLt + 1];
       if (!prim_setup(b, k, ci.E, ci.F, ci.Lt, omega, omega2, boys, c, Gm)) continue;
       ++any;
-      if constexpr (sizeof(R) == 4) {
-        const CoefRgT<float> cf = coef_f32(c, ci.E, ci.F);
-        for (int m = 0; m <= ci.Lt; ++m) V[m * sts] = to_f32(Gm[m]);
-        for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
-          const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-          for (int o = 0; o < n; ++o) vrr_bra<true>(ld_op(kVrrOps, off + o), V, S, sts, cf);
-        }
-        for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
-          const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-          for (int o = 0; o < n; ++o) vrr_ket<true>(ld_op(kVrrOps, off + o), V, S, sts, cf);
-        }
-      } else {
-        for (int m = 0; m <= ci.Lt; ++m) V[m * sts] = Gm[m];
-        for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
-          const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-          for (int o = 0; o < n; ++o) vrr_bra<true>(ld_op(kVrrOps, off + o), V, S, sts, c);
-        }
-        for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
-          const int off = ci.lv_off[lv], n = ci.lv_n[lv];
-          for (int o = 0; o < n; ++o) vrr_ket<true>(ld_op(kVrrOps, off + o), V, S, sts, c);
-        }
+      for (int m = 0; m <= ci.Lt; ++m) V[m * sts] = Gm[m];
+      for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
+        const int off = ci.lv_off[lv], n = ci.lv_n[lv];
+        for (int o = 0; o < n; ++o) vrr_bra<true>(ld_op(kVrrOps, off + o), V, S, sts, c);
+      }
+      for (int lv = ci.n_bra_lv; lv < ci.n_bra_lv + ci.n_ket_lv; ++lv) {
+        const int off = ci.lv_off[lv], n = ci.lv_n[lv];
+        for (int o = 0; o < n; ++o) vrr_ket<true>(ld_op(kVrrOps, off + o), V, S, sts, c);
       }
       for (int a = 0; a < ci.n_accl; ++a) {
         const uint32_t w = __ldg(kAccSrc + ci.acc_off + a);
@@ -211,6 +268,12 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedV
   return any;
 }
 
+// Position of set bit number n (0-based, from the least significant) of m; -1 if m has fewer.
+__device__ __forceinline__ int nth_bit(unsigned m, int n) {
+  for (int i = 0; i < n; ++i) m &= m - 1u;
+  return __ffs(m) - 1;
+}
+
 // Packed FP32 (mixed precision): every slot and coefficient holds two primitive quartets'
 // values (a float2), so one op of the schedule advances two primitive quartets with one
 // 64-bit load per operand and one FFMA2.  The slots have the FP64 layout (8 bytes each);
@@ -237,22 +300,8 @@ __device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const Sch
   const uint4* sched = reinterpret_cast<const uint4*>(kSched) + sv.off;
   const int npq = nb * nk;
   int any = 0;
-  for (int base = 0; base < npq; base += 32) {
-    const int t = base + lane;
-    double G[kMaxLt + 1];
-    PrimScalars ps;
-    int ib = 0, ik = 0;
-    bool ok = false;
-    if (t < npq) {
-      ib = t / nk;
-      ik = t - ib * nk;
-      ok = prim_core(pb[ib], pk[ik], ci.Lt, omega, omega2, boys, G, ps);
-    }
-    const unsigned okm = __ballot_sync(0xffffffffu, ok);
-    const int pos = __popc(okm & ((1u << lane) - 1u));
-    if (ok)
-      write_set<float, 2>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps,
-                          reinterpret_cast<float*>(CF + (pos >> 1) * HFX_NCOEF) + (pos & 1));
+  // the sets of the lanes in okm (at most 32) are in CF: run the schedule over them
+  auto run_sets = [&](unsigned okm) {
     const int nv = __popc(okm);
     any += nv;
     if (nv & 1)  // the second half of the last pair: an all-zero primitive quartet
@@ -273,6 +322,62 @@ __device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const Sch
         e = en;
       }
     }
+  };
+  // the primitive quartets c0 + (bits of m0, m1 << 32, m2 << 64) set up in FP64, 32 at a time
+  auto fp64_sets = [&](unsigned m0, unsigned m1, unsigned m2, int c0) {
+    const int n0 = __popc(m0), n1 = __popc(m1), nf = n0 + n1 + __popc(m2);
+    for (int base = 0; base < nf; base += 32) {
+      const int idx = base + lane;
+      bool ok = false;
+      int ib = 0, ik = 0;
+      double G[kMaxLt + 1];
+      PrimScalars ps;
+      if (idx < nf) {
+        const int u = idx < n0 ? nth_bit(m0, idx) : (idx < n0 + n1 ? 32 + nth_bit(m1, idx - n0) : 64 + nth_bit(m2, idx - n0 - n1));
+        const int t = c0 + u;
+        if (u >= 0 && t < npq) {
+          ib = t / nk;
+          ik = t - ib * nk;
+          ok = prim_core(pb[ib], pk[ik], ci.Lt, omega, omega2, boys, G, ps);
+        }
+      }
+      const unsigned okm = __ballot_sync(0xffffffffu, ok);
+      const int pos = __popc(okm & ((1u << lane) - 1u));
+      if (ok)
+        write_set<float, 2>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps,
+                            reinterpret_cast<float*>(CF + (pos >> 1) * HFX_NCOEF) + (pos & 1));
+      run_sets(okm);
+    }
+  };
+  // FP32 set-up first (prim_core_f32); the primitive quartets it declines are set up in FP64 at
+  // the end of their chunk of 96 (three rounds), 32 at a time, so that the FP64 set-up runs
+  // once per 32 of them rather than in every round in which one lane needs it
+  const float omega_f = to_f32(omega);
+  for (int c0 = 0; c0 < npq; c0 += 96) {
+    unsigned fm[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int base = c0 + 32 * r;
+      if (base >= npq) break;
+      const int t = base + lane;
+      float G[kMaxLt + 1];
+      PrimScalarsF ps;
+      int ib = 0, ik = 0, stt = F32_SKIP;
+      if (t < npq) {
+        ib = t / nk;
+        ik = t - ib * nk;
+        stt = prim_core_f32(pb[ib], pk[ik], ci.Lt, omega_f, G, ps);
+      }
+      fm[r] = __ballot_sync(0xffffffffu, stt == F32_FP64);
+      const bool ok = stt == F32_OK;
+      const unsigned okm = __ballot_sync(0xffffffffu, ok);
+      const int pos = __popc(okm & ((1u << lane) - 1u));
+      if (ok)
+        write_set_f32<2>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps,
+                         reinterpret_cast<float*>(CF + (pos >> 1) * HFX_NCOEF) + (pos & 1));
+      run_sets(okm);
+    }
+    if (fm[0] | fm[1] | fm[2]) fp64_sets(fm[0], fm[1], fm[2], c0);
   }
   if (!any) return 0;
   for (int a = lane; a < nacc; a += 32) {
