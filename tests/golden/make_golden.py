@@ -6,7 +6,7 @@ touches the CUDA library.  Run from the repository root:
     python tests/golden/make_golden.py diamond64    # 64-atom diamond, DZP-like (~ 20 min)
     python tests/golden/make_golden.py diamond96    # 96-atom piece of the 216-atom diamond (~ 1 h)
     python tests/golden/make_golden.py diamond216   # 216-atom diamond: K blocks only (~ 3 min)
-    python tests/golden/make_golden.py batch32      # the 32-system batch: K blocks only (~ 3 min)
+    python tests/golden/make_golden.py batch32      # the 32-system batch: K blocks only (~ 8 min)
 
 Output: tests/golden/oracle_<name>.json.  diamond64 and diamond96: E_K = tr(PK), per-class
 counts of kept canonical quartets, norms of K and a seeded sample of K blocks of the full
@@ -75,7 +75,7 @@ def main(name):
     if name == "diamond216":
         return blocks_only(name, [inputs.config3()], 24, 24, 21600)
     if name == "batch32":
-        return blocks_only(name, inputs.config2_systems(), 2, 1, 3200)
+        return blocks_only(name, inputs.config2_systems(), 4, 4, 3200)
     s, P = CASES[name]()
     B = oracle.Basis(s)
     t0 = time.time()

@@ -6,7 +6,12 @@ per-class counts of kept quartets):
   precision (K blocks within 1e-7; E_K within 1e-7 of the FP64 build, whose own E_K is
   pinned by the smaller parity tests);
 * the 32-system batch (8..128 atoms) in one batched build replayed from a CUDA graph,
-  the launch configuration bench.py times for it (K blocks of every system within 1e-10).
+  the launch configuration bench.py times for it (K blocks of every system within 1e-10);
+* the first 96 sites of the 216-atom generator, small enough for a full oracle K
+  (tests/golden/oracle_diamond96.json): E_K of the FP64 build within 1e-10 and of the
+  mixed-precision build within 1e-7 of the oracle's, K blocks likewise.
+The stored 216-atom blocks cover every pair of shell types (s, p, d) x (s, p, d), so every
+quartet class contributes to them.
 """
 import json
 import os
@@ -61,6 +66,27 @@ def test_diamond216_fp64_and_mixed(hfx_mod):
     print(f"diamond216 mixed: max|dK| blocks {mx:.2e} rms {rms:.2e}, |dE| vs FP64 {dE:.2e}")
     assert mx <= 1e-7 and dE <= 1e-7
     assert np.array_equal(out["fp64"][0], out["fp64"][0].T)
+
+
+def test_diamond96_energy_against_full_oracle(hfx_mod):
+    g = json.load(open(os.path.join(GOLD, "oracle_diamond96.json")))
+    s, P = inputs.config3(96)
+    assert s.n_bf == g["n_bf"] and s.seed == g["seed"]
+    Pd = torch.from_numpy(P).cuda()
+    for name, prec, tol in (("fp64", hfx_mod.HFX_FP64, 1e-10), ("mixed", hfx_mod.HFX_MIXED, 1e-7)):
+        h = hfx_mod.HFX(s, precision=prec).build_pairs()
+        st = h.stats()
+        assert st["n_quartets"] == g["n_quartets"]
+        assert st["n_quartets_class"] == g["n_quartets_class"]
+        K = h.build_K(Pd)
+        torch.cuda.synchronize()
+        Kh = K.cpu().numpy()
+        e = h.energy()
+        mx, rms = block_errors(s, Kh, g["blocks"])
+        print(f"diamond96 {name}: |dE| vs oracle {abs(e - g['E_K']):.2e}, max|dK| blocks {mx:.2e}")
+        assert abs(e - g["E_K"]) <= tol
+        assert mx <= tol
+        h.close()
 
 
 def test_batch32_graph(hfx_mod):
