@@ -109,19 +109,7 @@ __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaun
       }
     }
   } else {
-    for (int t = 0; t < npq; ++t) {
-      const int ib = t / nk, ik = t - ib * nk;
-      const PrimPair b = pb[ib];
-      PrimPair k = pk[ik];
-      if constexpr (PER) {  // the ket pair's image in cell G (its centre moves, P - C does not)
-        k.P[0] += L.shift[0];
-        k.P[1] += L.shift[1];
-        k.P[2] += L.shift[2];
-      }
-      CoefRg c;
-      double Gm[kMaxLt + 1];
-      if (!prim_setup(b, k, ci.E, ci.F, ci.Lt, omega, omega2, boys, c, Gm)) continue;
-      ++any;
+    auto vrr = [&](const CoefRg& c, const double* Gm) {
       for (int m = 0; m <= ci.Lt; ++m) V[m * sts] = Gm[m];
       for (int lv = 0; lv < ci.n_bra_lv; ++lv) {
         const int off = ci.lv_off[lv], n = ci.lv_n[lv];
@@ -135,6 +123,23 @@ __device__ __forceinline__ int contract_g1(const EriClassInfo& ci, const EriLaun
         const uint32_t w = __ldg(kAccSrc + ci.acc_off + a);
         S[(w & 0xFFFF) * sts] += V[(w >> 16) * sts];
       }
+    };
+    auto ket_of = [&](int ik) {
+      PrimPair k = pk[ik];
+      if constexpr (PER) {  // the ket pair's image in cell G (its centre moves, P - C does not)
+        k.P[0] += L.shift[0];
+        k.P[1] += L.shift[1];
+        k.P[2] += L.shift[2];
+      }
+      return k;
+    };
+    for (int t = 0; t < npq; ++t) {
+      const int ib = t / nk, ik = t - ib * nk;
+      CoefRg c;
+      double Gm[kMaxLt + 1];
+      if (!prim_setup(pb[ib], ket_of(ik), ci.E, ci.F, ci.Lt, omega, omega2, boys, c, Gm)) continue;
+      ++any;
+      vrr(c, Gm);
     }
   }
   if (!any) return 0;
