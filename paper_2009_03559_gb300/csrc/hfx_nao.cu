@@ -14,7 +14,9 @@
 //
 // Gaussians on the grid: for an exponent a and beta = a h^2, exp(-beta i^2) moves along one lane's
 // points (i -> i + 32) by the factor exp(-beta (64 i + 1024)), and that factor by exp(-2048 beta):
-// three exp() calls per Gaussian and lane, then two multiplies per point.
+// two exp() calls per Gaussian and lane plus the lane-independent one, then two multiplies per
+// point.  In the genetic step an individual's alpha = exp(u) and exp(-2048 beta) are made once,
+// by the lane that makes the individual, and kept with its genes.
 //
 // The paper names the two searches but does not spell them out; the readings (shared with the
 // CPU reference the tests compare against) are:
@@ -36,6 +38,7 @@
 //    (0: the initial population) of restart q is ((q (G + 1) + g) P + j) (4 + 2M) + k.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -54,7 +57,8 @@ constexpr int kMatLd = kMaxUnknowns + 1;
 constexpr int kMatDoubles = kMaxUnknowns * kMatLd + kMatLd;  // matrix + right-hand side
 constexpr int kMaxNr = 1024;
 constexpr int kMaxPop = 64;
-constexpr int kWarps = 4;  // warps (restarts) per block
+constexpr int kWarps = 4;  // warps (restarts) per block at most
+constexpr size_t kMaxBlockSmem = 227 * 1024;
 
 constexpr double kRidge = 1e-12;
 constexpr double kTieFactor = 1.0 - 1e-12;
@@ -91,14 +95,19 @@ __host__ __device__ constexpr int n_tri(int m) { return m * (m + 1) / 2; }
 __host__ __device__ constexpr int n_red(int m) { return 3 * n_tri(m) + 2 * m + 1; }
 
 __host__ __device__ inline int warp_smem_doubles(int M, int npad, int P) {
-  return npad + n_red(M) * 33 + kMatDoubles + 2 * P * M + 2 * P;
+  return npad + n_red(M) * 33 + kMatDoubles + 10 * P * M + 2 * P;
 }
 
+// pop: genes u_m = ln alpha_m; al: alpha_m; fac: per Gaussian exp(-beta), exp(-64 beta) and
+// exp(-1024 beta), beta = alpha_m h^2, the factors of the grid recurrence (made once per
+// individual by the lane that makes it)
 struct WarpMem {
   double* y;
   double* red;
   double* mat;
   double* pop[2];
+  double* al[2];
+  double* fac[2];
   double* fit[2];
 };
 
@@ -112,7 +121,11 @@ __device__ __forceinline__ WarpMem warp_mem(int M, int npad, int P) {
   m.mat = m.red + n_red(M) * 33;
   m.pop[0] = m.mat + kMatDoubles;
   m.pop[1] = m.pop[0] + P * M;
-  m.fit[0] = m.pop[1] + P * M;
+  m.al[0] = m.pop[1] + P * M;
+  m.al[1] = m.al[0] + P * M;
+  m.fac[0] = m.al[1] + P * M;
+  m.fac[1] = m.fac[0] + 3 * P * M;
+  m.fit[0] = m.fac[1] + 3 * P * M;
   m.fit[1] = m.fit[0] + P;
   return m;
 }
@@ -186,6 +199,16 @@ __device__ __forceinline__ double warp_sum1(double v) {
   return __shfl_sync(0xffffffffu, v, 0);  // lane 0's order for everyone
 }
 
+// inclusive product of v over lanes 0..lane
+__device__ __forceinline__ double scan_mul(double v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v *= t;
+  }
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // Gaussians along one lane's grid points
 // ---------------------------------------------------------------------------
@@ -200,6 +223,20 @@ struct LaneGauss {
       e[m] = exp(-beta * (i0 * i0));
       c[m] = exp(-beta * (64.0 * i0 + 1024.0));
       d[m] = exp(-2048.0 * beta);
+    }
+  }
+  // the same from the lane-independent factors f = (exp(-beta), exp(-64 beta), exp(-1024 beta))
+  // per Gaussian, by product scans over the lanes: with a = exp(-beta), lane j's first point
+  // i0 = j + 1 has exp(-beta i0^2) = prod_{k <= j} a^{2k+1} and exp(-beta (64 i0 + 1024)) =
+  // exp(-1024 beta) exp(-64 beta)^{j+1}; the step factor is exp(-1024 beta)^2
+  __device__ __forceinline__ void init_scan(const double* f, int lane) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const double a = f[3 * m], q = f[3 * m + 1], s = f[3 * m + 2];
+      const double r = a * scan_mul(lane == 0 ? 1.0 : a * a, lane);  // a^{2 lane + 1}
+      e[m] = scan_mul(r, lane);
+      c[m] = s * scan_mul(q, lane);
+      d[m] = s * s;
     }
   }
   __device__ __forceinline__ void step() {
@@ -241,9 +278,7 @@ __device__ __forceinline__ bool chol_solve_reg(double (&a)[n_tri(N)], double (&b
 #pragma unroll
     for (int k = 0; k < j; ++k) s = fma(-a[n_tri(j) + k], a[n_tri(j) + k], s);
     if (!(s > 0.0)) return false;
-    const double dj = sqrt(s);
-    rd[j] = 1.0 / dj;
-    a[n_tri(j) + j] = dj;
+    rd[j] = rsqrt(s);  // the solves need only 1 / L_jj
 #pragma unroll
     for (int i = j + 1; i < N; ++i) {
       double t = a[n_tri(i) + j];
@@ -272,10 +307,13 @@ __device__ __forceinline__ bool chol_solve_reg(double (&a)[n_tri(N)], double (&b
 // Variable projection: D minimising err for fixed alpha (ridged normal equations), and err there.
 template <int M>
 __device__ __forceinline__ double project(const double (&alpha)[M], double (&D)[M], const NaoArgs& A,
-                                          const WarpMem& wm, int lane) {
+                                          const WarpMem& wm, int lane, const double* fac = nullptr) {
   constexpr int NA = n_tri(M);
   LaneGauss<M> g0;
-  g0.init(alpha, A.h * A.h, lane);
+  if (fac)
+    g0.init_scan(fac, lane);
+  else
+    g0.init(alpha, A.h * A.h, lane);
   LaneGauss<M> g = g0;
   double acc[NA + M];
 #pragma unroll
@@ -346,18 +384,34 @@ __device__ __forceinline__ double reflect_box(double c, double lo, double hi) {
 }
 
 template <int M>
-__device__ __forceinline__ double eval_individual(const double* genes, const NaoArgs& A, const WarpMem& wm,
-                                                  int lane) {
+__device__ __forceinline__ double eval_individual(const double* al, const double* fac, const NaoArgs& A,
+                                                  const WarpMem& wm, int lane) {
   double alpha[M], D[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) alpha[m] = exp(genes[m]);
-  return project<M>(alpha, D, A, wm, lane);
+  for (int m = 0; m < M; ++m) alpha[m] = al[m];
+  return project<M>(alpha, D, A, wm, lane, fac);
+}
+
+// alpha = exp(u) and the grid-recurrence factors of one individual, into shared memory
+template <int M>
+__device__ __forceinline__ void store_individual(const double (&u)[M], double h2, double* pop, double* al,
+                                                 double* fac) {
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const double a = exp(u[m]);
+    const double beta = a * h2;
+    pop[m] = u[m];
+    al[m] = a;
+    fac[3 * m] = exp(-beta);
+    fac[3 * m + 1] = exp(-64.0 * beta);
+    fac[3 * m + 2] = exp(-1024.0 * beta);
+  }
 }
 
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32) nao_genetic_kernel(NaoArgs A) {
   const int lane = threadIdx.x & 31;
-  const long long q = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const long long q = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (q >= (long long)A.n_fun * A.N) return;  // whole warps leave together
   const int f = (int)(q / A.N);
   const int P = A.P, G = A.G;
@@ -369,18 +423,18 @@ __global__ void __launch_bounds__(kWarps * 32) nao_genetic_kernel(NaoArgs A) {
             (unsigned long long)j) * (unsigned long long)S + (unsigned long long)k;
   };
   const double span = __dsub_rn(A.hi, A.lo);
+  const double h2 = A.h * A.h;
   // initial population
   for (int j = lane; j < P; j += 32) {
     double u[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) u[m] = __dadd_rn(A.lo, __dmul_rn(uniform01(A.seed, ctr(0, j, m)), span));
     sort_genes<M>(u);
-#pragma unroll
-    for (int m = 0; m < M; ++m) wm.pop[0][j * M + m] = u[m];
+    store_individual<M>(u, h2, wm.pop[0] + j * M, wm.al[0] + j * M, wm.fac[0] + 3 * j * M);
   }
   __syncwarp();
   for (int j = 0; j < P; ++j) {
-    const double fj = eval_individual<M>(wm.pop[0] + j * M, A, wm, lane);
+    const double fj = eval_individual<M>(wm.al[0] + j * M, wm.fac[0] + 3 * j * M, A, wm, lane);
     if (lane == 0) wm.fit[0][j] = fj;
   }
   __syncwarp();
@@ -389,12 +443,18 @@ __global__ void __launch_bounds__(kWarps * 32) nao_genetic_kernel(NaoArgs A) {
     const double* pop = wm.pop[cur];
     const double* fit = wm.fit[cur];
     double* npop = wm.pop[cur ^ 1];
+    double* nal = wm.al[cur ^ 1];
+    double* nfac = wm.fac[cur ^ 1];
     double* nfit = wm.fit[cur ^ 1];
     const int e = best_index(fit, P);
     for (int j = lane; j < P; j += 32) {
       if (j == 0) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) npop[m] = pop[e * M + m];
+        for (int m = 0; m < M; ++m) {
+          npop[m] = pop[e * M + m];
+          nal[m] = wm.al[cur][e * M + m];
+          for (int k = 0; k < 3; ++k) nfac[3 * m + k] = wm.fac[cur][3 * (e * M + m) + k];
+        }
         nfit[0] = fit[e];
         continue;
       }
@@ -418,12 +478,11 @@ __global__ void __launch_bounds__(kWarps * 32) nao_genetic_kernel(NaoArgs A) {
         c[m] = reflect_box(v, A.lo, A.hi);
       }
       sort_genes<M>(c);
-#pragma unroll
-      for (int m = 0; m < M; ++m) npop[j * M + m] = c[m];
+      store_individual<M>(c, h2, npop + j * M, nal + j * M, nfac + 3 * j * M);
     }
     __syncwarp();
     for (int j = 1; j < P; ++j) {
-      const double fj = eval_individual<M>(npop + j * M, A, wm, lane);
+      const double fj = eval_individual<M>(nal + j * M, nfac + 3 * j * M, A, wm, lane);
       if (lane == 0) nfit[j] = fj;
     }
     __syncwarp();
@@ -432,8 +491,8 @@ __global__ void __launch_bounds__(kWarps * 32) nao_genetic_kernel(NaoArgs A) {
   const int e = best_index(wm.fit[cur], P);
   double alpha[M], D[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) alpha[m] = exp(wm.pop[cur][e * M + m]);
-  const double fe = project<M>(alpha, D, A, wm, lane);
+  for (int m = 0; m < M; ++m) alpha[m] = wm.al[cur][e * M + m];
+  const double fe = project<M>(alpha, D, A, wm, lane, wm.fac[cur] + 3 * e * M);
   if (lane == 0) {
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -487,7 +546,7 @@ __device__ bool chol_solve_smem(double* mat, int n, int lane) {
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32) nao_local_kernel(NaoArgs A) {
   const int lane = threadIdx.x & 31;
-  const long long q = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const long long q = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (q >= (long long)A.n_fun * A.N) return;
   const int f = (int)(q / A.N);
   constexpr int NA = n_tri(M);
@@ -684,7 +743,7 @@ __global__ void nao_best_kernel(int n_fun, int N, int M, const double* r_alpha, 
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32) nao_project_kernel(NaoArgs A) {
   const int lane = threadIdx.x & 31;
-  const long long s = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const long long s = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (s >= A.n_set) return;
   const int f = __ldg(A.fun_of_set + s);
   if (f < 0 || f >= A.n_fun) {  // no such function: NaN out, nothing read
@@ -735,16 +794,19 @@ const void* kernel_for(int M, Which w) {
 
 int launch(Which w, int M, const NaoArgs& a, long long n_warps, cudaStream_t s) {
   if (n_warps <= 0) return HFX_OK;
-  const size_t smem = (size_t)kWarps * warp_smem_doubles(M, a.npad, a.P) * sizeof(double);
+  // up to kWarps restarts per block, as many as the shared memory of a block holds
+  const size_t per_warp = (size_t)warp_smem_doubles(M, a.npad, a.P) * sizeof(double);
+  const int warps = (int)std::max<size_t>(1, std::min<size_t>(kWarps, kMaxBlockSmem / per_warp));
+  const size_t smem = warps * per_warp;
   const void* k = kernel_for(M, w);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) {
     hfx::set_global_error(std::string("nao: shared memory request refused: ") + cudaGetErrorString(e));
     return HFX_ERR_CUDA;
   }
-  const long long blocks = (n_warps + kWarps - 1) / kWarps;
+  const long long blocks = (n_warps + warps - 1) / warps;
   void* args[] = {(void*)&a};
-  e = cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(kWarps * 32), args, smem, s);
+  e = cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
   if (e != cudaSuccess) {
     hfx::set_global_error(std::string("nao: launch failed: ") + cudaGetErrorString(e));
     return HFX_ERR_CUDA;

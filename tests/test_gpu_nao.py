@@ -168,3 +168,19 @@ def test_empty_and_default_workload_sampled(fitter):
         assert out["err"][f] == out["r_err"][f * 512:(f + 1) * 512].min()
         y = N.targets(rs.phi[f], int(rs.l[f]), rs.h)
         assert out["err"][f] == pytest.approx(N.err(out["alpha"][f], out["D"][f], y, r), rel=1e-10)
+
+
+def test_largest_options(fitter):
+    """M = 6 Gaussians, population 64, n_r = 1024 (fewer restarts per block: shared memory)."""
+    hfx, _, _ = fitter
+    n_r, h = 1024, 6.0 / 1024
+    r = N.grid(n_r, h)
+    phi = (r ** 2 * np.exp(-1.1 * r) * (1 - (r / 6.0) ** 2) ** 2)[None, :]
+    F = hfx.NAOFit(phi, [2], h)
+    o = hfx.nao_options(n_gauss=6, n_restarts=3, population=64, generations=2, max_iter=30, seed=8)
+    out = {k: v.cpu().numpy() for k, v in F.fit(o).items()}
+    ref = N.fit(phi[0], 2, h, M=6, N=3, P=64, G=2, max_iter=30, seed=8)
+    for it, p in enumerate(ref["restarts"]):
+        assert out["r_ga_err"][it] == pytest.approx(N.err(p["ga_alpha"], p["ga_D"], N.targets(phi[0], 2, h), r),
+                                                    rel=1e-8)
+    assert out["err"][0] == pytest.approx(ref["best"]["err"], rel=1e-6)
