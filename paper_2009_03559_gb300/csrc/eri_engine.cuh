@@ -15,6 +15,7 @@
 //      A_bd += sum_ac v P_ac, with v = deg (ab|cd), deg = 1/2^[a=b] 1/2^[c=d] 1/2^[ab=cd].
 // The per-class op lists come from gen_eri_tables.py (eri_tables.inc).
 #pragma once
+#include <type_traits>
 #include "hfx_internal.cuh"
 
 namespace hfx {
@@ -404,7 +405,8 @@ __device__ __forceinline__ void sched_op(uint4 e, R* S, int rsz, int zero, const
   if (!(w & (1u << 10))) return;
   const int u = (w >> 13) & 7;
   const int p = j + u;
-  const R* cf = CF + (p < nv ? p : 32) * HFX_NCOEF;
+  // past the last set: the all-zero set (32; 16 in the packed FP32 layout)
+  const R* cf = CF + (p < nv ? p : (std::is_same<R, float2>::value ? 16 : 32)) * HFX_NCOEF;
   R* X = S + u * rsz;
   const int base = (w & (1u << 7)) ? HFX_CF_KET_BASE : 0;
   const int dir = w & 3;

@@ -182,8 +182,9 @@ __device__ __forceinline__ void post_stages(const EriClassInfo& ci, const PairAr
 
 // Group scratch of one warp (in doubles): k stream regions, 33 coefficient sets (the last
 // one all zeros), one spare double.
-__host__ __device__ __forceinline__ int g32_stride(const SchedVariant& sv) {
-  return sv.group + 33 * HFX_NCOEF + 1;
+__host__ __device__ __forceinline__ int g32_stride(const SchedVariant& sv, int prec = 0) {
+  // the packed FP32 pass holds two primitive quartets per set: 16 sets and the zero set
+  return sv.group + (prec == 2 ? 17 : 33) * HFX_NCOEF + 1;
 }
 
 template <typename R, bool PER = false>
@@ -301,7 +302,7 @@ __device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const Sch
     S[u * rsz + (i - u * nacc)] = z2;
   }
   if (lane < k) S[lane * rsz + sv.zero] = z2;
-  for (int i = lane; i < HFX_NCOEF; i += 32) CF[32 * HFX_NCOEF + i] = z2;
+  for (int i = lane; i < HFX_NCOEF; i += 32) CF[16 * HFX_NCOEF + i] = z2;
   const uint4* sched = reinterpret_cast<const uint4*>(kSched) + sv.off;
   const int npq = nb * nk;
   int any = 0;
@@ -413,6 +414,9 @@ __device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const Sch
 #endif
 #ifndef HFX_G32B_MINB
 #define HFX_G32B_MINB 8
+#endif
+#ifndef HFX_G32F_MINB  // packed FP32 pass: 10 or 12 blocks spill (64-atom mixed build 3354 / 3309 ms vs 3021)
+#define HFX_G32F_MINB 8
 #endif
 
 // Precision passes of a class launch: 0 every quartet in FP64; 1 (mixed precision, first
@@ -841,11 +845,12 @@ __global__ void __launch_bounds__(64, PREC == PREC_MIXED32 ? HFX_G1F_MINB : (BAT
 }
 
 template <int MODE, int PREC, bool BATCH, bool PER = false>
-__global__ void __launch_bounds__(64, BATCH ? HFX_G32B_MINB : HFX_G32_MINB) eri_g32_kernel(const EriLaunch L) {
+__global__ void __launch_bounds__(64, BATCH ? HFX_G32B_MINB : (PREC == PREC_MIXED32 ? HFX_G32F_MINB : HFX_G32_MINB))
+    eri_g32_kernel(const EriLaunch L) {
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int gpb = blockDim.x >> 5;
-  double* S = smem + grp * g32_stride(L.sv);
+  double* S = smem + grp * g32_stride(L.sv, PREC);
   double* CF = S + L.sv.group;
   const long long gid = (long long)blockIdx.x * gpb + grp;
   const long long ng = (long long)gridDim.x * gpb;
@@ -941,12 +946,12 @@ static const void* kernel_ptr(int mode, int gs, int prec, bool batch) {
 
 static int effective_gs(int gs) { return gs == 1 ? 1 : 32; }
 
-size_t eri_smem_bytes(int cls, int gs, int streams) {
+size_t eri_smem_bytes(int cls, int gs, int streams, int prec) {
   // one quartet per thread: interleaved scratch, then a 64-entry quartet queue per warp
   if (gs == 1) return sizeof(double) * (size_t)kClassInfo[cls].scratch * kBlock + sizeof(int4) * 64 * (kBlock / 32);
   const int i = variant_index(cls, streams);
   if (i < 0) return (size_t)1 << 30;
-  return sizeof(double) * (size_t)g32_stride(kSchedInfo[cls][i]) * (kBlock / 32);
+  return sizeof(double) * (size_t)g32_stride(kSchedInfo[cls][i], prec) * (kBlock / 32);
 }
 
 int eri_block_size() { return kBlock; }
@@ -977,7 +982,7 @@ int eri_blocks_per_sm(int cls, int mode, int gs, int prec, bool batch, int strea
   int n = 0;
   const int g = effective_gs(gs);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_ptr(mode, g, prec, batch), kBlock,
-                                                    eri_smem_bytes(cls, g, streams)) != cudaSuccess)
+                                                    eri_smem_bytes(cls, g, streams, prec)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }
@@ -987,7 +992,7 @@ int eri_groups_per_block(int gs) { return kBlock / effective_gs(gs); }
 cudaError_t eri_launch(const EriLaunch& L0, int cls, int mode, int grid, cudaStream_t stream, int gs, int prec,
                        bool batch, int streams) {
   const int g = effective_gs(gs);
-  const size_t smem = eri_smem_bytes(cls, g, streams);
+  const size_t smem = eri_smem_bytes(cls, g, streams, prec);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   const void* k = kernel_ptr(mode, g, prec, batch);
   EriLaunch L = L0;

@@ -11,7 +11,7 @@ struct EriLaunch;
 // 0 every quartet in FP64; 1 and 2 the FP64 and FP32 shares of a mixed-precision class.
 int eri_group_size(int cls);  // default for a class: 1 or 32
 bool eri_group_size_valid(int gs);
-size_t eri_smem_bytes(int cls, int gs, int streams = 0);
+size_t eri_smem_bytes(int cls, int gs, int streams = 0, int prec = 0);
 int eri_block_size();
 cudaError_t eri_prepare();
 int eri_blocks_per_sm(int cls, int mode, int gs, int prec, bool batch, int streams = 0);
