@@ -246,9 +246,11 @@ int hfx_energy(hfx_ctx* ctx, double* out);
 int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out);
 
 /* Lanes per quartet for class cls (0..20) in later K builds of this context: 1 (a thread
- * owns a quartet), 32 (a warp), 0 = the library's default.  Mixed-precision classes always
- * run 32; 1 needs a class whose scratch fits the thread kernel (the classes that default to
- * 1), else the build fails with HFX_ERR_CUDA.  Errors: HFX_ERR_ARG. */
+ * owns a quartet), 32 (a warp), 0 = the library's default (1 for the nine classes whose
+ * scratch fits the thread kernel, 32 otherwise; in a mixed-precision build the FP32 pass runs
+ * 32 in every class).  A value set here applies to both passes of a mixed-precision class.
+ * 1 needs a class whose scratch fits the thread kernel, else the build fails with
+ * HFX_ERR_CUDA.  Errors: HFX_ERR_ARG. */
 int hfx_set_group_size(hfx_ctx* ctx, int cls, int gs);
 
 /* Enables (1) or disables (0) per-class CUDA-event timing of K builds. */

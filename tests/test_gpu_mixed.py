@@ -1,8 +1,10 @@
-"""Mixed precision: FP32 recurrences for quartets with Q_IJ Q_KL max|P blocks| < 1e-6,
-FP64 Boys step, HRR and K accumulation.  Tolerance against the FP64 oracle: max |dK| <=
-1e-7 and |dE_K| <= 1e-7 Hartree (the number the target statement fixes for this path).
-The class masks checked: the default (13 warp-group classes, (dd|dd) kept FP64), s,p
-classes only, and all classes (on the small cases, where it still meets the tolerance)."""
+"""Mixed precision: FP32 set-up (incomplete-gamma Boys step, FP64 for the primitive quartets it
+declines), recurrences and contraction for quartets with Q_IJ Q_KL max|P blocks| < 1e-6; FP64
+HRR, spherical step and K accumulation.  Tolerance against the FP64 oracle: max |dK| <= 1e-7 and
+|dE_K| <= 1e-7 Hartree (the number the target statement fixes for this path).  The class masks
+checked: the default (every class but (dd|dd)), s,p classes only, and all classes (on the small
+cases, where it still meets the tolerance).  Shells of 5 and 6 primitives run the primitive
+loops in several chunks of 96 (the deferred FP64 set-ups are flushed per chunk)."""
 import json
 import os
 
@@ -96,3 +98,22 @@ def test_mixed_global_pmax(hfx_mod, case):
           f"max|dK| {np.abs(Kg - Ko).max():.2e} |dE| {abs(eg - eo):.2e}")
     assert 0 < ng <= nq
     assert np.abs(Kg - Ko).max() <= TOL and abs(eg - eo) <= TOL
+
+
+@pytest.mark.parametrize("kind,nprim", [("diamond", 5), ("cluster", 6)])
+def test_many_primitives(hfx_mod, kind, nprim):
+    """More than 96 primitive quartets per quartet (up to 25 x 25 or 36 x 36): FP64 and mixed
+    builds against the oracle."""
+    if kind == "diamond":
+        s = inputs.diamond_system(4, seed=71, nprim=nprim, tau=1e-8, rcut=6.0)
+        P = inputs.density_matrix(s, truncate_bohr=10.0)
+    else:
+        s = inputs.cluster_system(6, seed=72, nprim=nprim, tau=1e-10, rcut=0.0)
+        P = inputs.density_matrix(s)
+    Ko, eo = oracle_K(s, P)
+    h, K, e = build(hfx_mod, s, P)
+    assert np.abs(K - Ko).max() <= 1e-10 and abs(e - eo) <= 1e-10
+    h, K, e = build(hfx_mod, s, P, precision=hfx_mod.HFX_MIXED)
+    st = h.stats()
+    assert sum(st["quartets_fp32_class"]) > 0
+    assert np.abs(K - Ko).max() <= TOL and abs(e - eo) <= TOL
