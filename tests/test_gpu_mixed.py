@@ -108,7 +108,7 @@ def test_many_primitives(hfx_mod, kind, nprim):
         s = inputs.diamond_system(4, seed=71, nprim=nprim, tau=1e-8, rcut=6.0)
         P = inputs.density_matrix(s, truncate_bohr=10.0)
     else:
-        s = inputs.cluster_system(6, seed=72, nprim=nprim, tau=1e-10, rcut=0.0)
+        s = inputs.cluster_system(8, seed=72, nprim=nprim, h=5.0, tau=1e-10, rcut=0.0)
         P = inputs.density_matrix(s)
     Ko, eo = oracle_K(s, P)
     h, K, e = build(hfx_mod, s, P)
