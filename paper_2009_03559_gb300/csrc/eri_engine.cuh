@@ -1,7 +1,8 @@
 // Table-driven engine for contracted shell quartets (ab|cd) with the erfc(omega r)/r
 // kernel, fused with the exchange-matrix digest.  It runs in FP64; the recurrence and
-// contraction steps are templated on the arithmetic type, so the mixed-precision kernel
-// runs them in FP32 for the quartets that qualify (the Boys step stays FP64).
+// contraction steps are templated on the arithmetic type, and an FP32 primitive set-up
+// (prim_core_f32) feeds them, so the mixed-precision kernel runs set-up, recurrences and
+// contraction in FP32 for the quartets that qualify (HRR, spherical step and digest in FP64).
 //
 // One "group" of G lanes (G = 1 or G = 32) evaluates one contracted quartet:
 //   1. for every surviving primitive quartet: the Boys step (G_m = F_m(T) -
