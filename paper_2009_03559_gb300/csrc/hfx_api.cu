@@ -816,13 +816,14 @@ extern "C" int hfx_get_stats(hfx_ctx* ctx, hfx_stats* out) {
       st.prim_quartets_class[cp] = (int64_t)c[0];
       st.quartets_evaluated_class[cp] = (int64_t)c[1];
       st.quartets_fp32_class[cp] = (int64_t)c[3];
-      // FP64: every set-up (Boys step), the recurrences of FP64 quartets, every digest;
-      // FP32: the recurrences of FP32 quartets
-      const double f64 = (double)c[0] * setup_flops(ci.E, ci.F, ci.Lt, ctx->opt.omega > 0.0) +
-                         (double)(c[0] - c[4]) * ci.flops_prim +
+      // FP64: the set-up and the recurrences of FP64 quartets, every digest; FP32: the set-up
+      // and the recurrences of FP32 quartets (the few primitive quartets whose Boys step the
+      // FP32 set-up declines are set up in FP64 but counted here as FP32)
+      const double su = setup_flops(ci.E, ci.F, ci.Lt, ctx->opt.omega > 0.0);
+      const double f64 = (double)(c[0] - c[4]) * (su + ci.flops_prim) +
                          (double)(c[1] - c[3]) * (ci.flops_quartet - ci.flops_digest) +
                          (double)c[1] * ci.flops_digest + (double)c[2] * skip_flops();
-      const double f32 = (double)c[4] * ci.flops_prim + (double)c[3] * (ci.flops_quartet - ci.flops_digest);
+      const double f32 = (double)c[4] * (su + ci.flops_prim) + (double)c[3] * (ci.flops_quartet - ci.flops_digest);
       st.flops_class[cp] = f64 + f32;
       fl += f64;
       fl32 += f32;
