@@ -35,6 +35,17 @@ __device__ __constant__ float kSphCoefF[6] = {0.0f, 1.0f, -0.28867513459481287f,
 __device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float2 fmar(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float4 fmar(float4 a, float4 b, float4 c) {
+  const float2 lo = __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(c.x, c.y));
+  const float2 hi = __ffma2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w), make_float2(c.z, c.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+// index of the all-zero coefficient set of a packed layout (32 sets of one primitive quartet,
+// 16 of two, 8 of four)
+template <typename R>
+__host__ __device__ constexpr int zero_set() {
+  return std::is_same<R, float4>::value ? 8 : (std::is_same<R, float2>::value ? 16 : 32);
+}
 template <typename R>
 __device__ __forceinline__ R sph_coef(int i);
 template <>
@@ -406,8 +417,8 @@ __device__ __forceinline__ void sched_op(uint4 e, R* S, int rsz, int zero, const
   if (!(w & (1u << 10))) return;
   const int u = (w >> 13) & 7;
   const int p = j + u;
-  // past the last set: the all-zero set (32; 16 in the packed FP32 layout)
-  const R* cf = CF + (p < nv ? p : (std::is_same<R, float2>::value ? 16 : 32)) * HFX_NCOEF;
+  // past the last set: the all-zero set
+  const R* cf = CF + (p < nv ? p : zero_set<R>()) * HFX_NCOEF;
   R* X = S + u * rsz;
   const int base = (w & (1u << 7)) ? HFX_CF_KET_BASE : 0;
   const int dir = w & 3;

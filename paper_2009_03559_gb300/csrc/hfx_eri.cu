@@ -180,11 +180,19 @@ __device__ __forceinline__ void post_stages(const EriClassInfo& ci, const PairAr
   }
 }
 
+// primitive quartets per slot of the packed FP32 pass (2: float2, 4: float4)
+#ifndef HFX_FP32_PACK
+#define HFX_FP32_PACK 4
+#endif
+
 // Group scratch of one warp (in doubles): k stream regions, 33 coefficient sets (the last
 // one all zeros), one spare double.
 __host__ __device__ __forceinline__ int g32_stride(const SchedVariant& sv, int prec = 0) {
-  // the packed FP32 pass holds two primitive quartets per set: 16 sets and the zero set
-  return sv.group + (prec == 2 ? 17 : 33) * HFX_NCOEF + 1;
+  // the packed FP32 pass holds two primitive quartets per set (16 sets and the zero set), or
+  // four (stream regions of twice the size, 8 sets and the zero set, in doubles twice 9 x NCOEF)
+  if (prec != 2) return sv.group + 33 * HFX_NCOEF + 1;
+  // float4 slots need 16-byte alignment: an even stride keeps every warp's region aligned
+  return HFX_FP32_PACK == 4 ? 2 * sv.group + 9 * HFX_NCOEF * 2 + 2 : sv.group + 17 * HFX_NCOEF + 1;
 }
 
 template <typename R, bool PER = false>
@@ -280,16 +288,34 @@ __device__ __forceinline__ int nth_bit(unsigned m, int n) {
   return __ffs(m) - 1;
 }
 
-// Packed FP32 (mixed precision): every slot and coefficient holds two primitive quartets'
-// values (a float2), so one op of the schedule advances two primitive quartets with one
-// 64-bit load per operand and one FFMA2.  The slots have the FP64 layout (8 bytes each);
-// the contracted block is widened in place to FP64 (the two halves summed in FP64) for the
-// horizontal recurrences, the spherical step and the digest.
-__device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const SchedVariant& sv, const EriLaunch& L,
+// Packed FP32 (mixed precision): every slot and coefficient holds W primitive quartets'
+// values (a float2 for W = 2, a float4 for W = 4), so one op of the schedule advances W
+// primitive quartets with one W-wide load per operand and W/2 FFMA2.  The stream regions hold
+// W floats per slot; the coefficient area holds 32/W sets and the zero set.  The contracted
+// block is widened to FP64 (the W components summed in FP64) for the horizontal recurrences,
+// the spherical step and the digest, which run on the FP64 view of the same memory.
+template <int W>
+struct PackV;
+template <>
+struct PackV<2> {
+  using T = float2;
+};
+template <>
+struct PackV<4> {
+  using T = float4;
+};
+
+template <int W>
+__device__ __forceinline__ int contract_g32_xw(const EriClassInfo& ci, const SchedVariant& sv, const EriLaunch& L,
                                                int bra, int ket, double* Sd, double* CFd, int lane) {
-  float2* S = reinterpret_cast<float2*>(Sd);
-  float2* CF = reinterpret_cast<float2*>(CFd);
-  const float2 z2 = make_float2(0.f, 0.f);
+  using V = typename PackV<W>::T;
+  constexpr int kZeroSet = 32 / W;
+  V* S = reinterpret_cast<V*>(Sd);
+  V* CF = reinterpret_cast<V*>(CFd);
+  V zv;
+  float* zf = reinterpret_cast<float*>(&zv);
+#pragma unroll
+  for (int c = 0; c < W; ++c) zf[c] = 0.f;
   const PairArrays pa = L.pa;
   const double omega = L.omega, omega2 = L.omega2;
   const double* boys = L.boys;
@@ -299,31 +325,37 @@ __device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const Sch
   const int k = sv.k, rsz = sv.rsz, nacc = ci.n_acc, nbase = ci.Lt + 1;
   for (int i = lane; i < k * nacc; i += 32) {
     const int u = i / nacc;
-    S[u * rsz + (i - u * nacc)] = z2;
+    S[u * rsz + (i - u * nacc)] = zv;
   }
-  if (lane < k) S[lane * rsz + sv.zero] = z2;
-  for (int i = lane; i < HFX_NCOEF; i += 32) CF[16 * HFX_NCOEF + i] = z2;
+  if (lane < k) S[lane * rsz + sv.zero] = zv;
+  for (int i = lane; i < HFX_NCOEF; i += 32) CF[kZeroSet * HFX_NCOEF + i] = zv;
   const uint4* sched = reinterpret_cast<const uint4*>(kSched) + sv.off;
   const int npq = nb * nk;
   int any = 0;
+  // component pos of the packed sets (pos < 32)
+  auto slot_of = [&](int pos) { return reinterpret_cast<float*>(CF + (pos / W) * HFX_NCOEF) + (pos % W); };
   // the sets of the lanes in okm (at most 32) are in CF: run the schedule over them
   auto run_sets = [&](unsigned okm) {
     const int nv = __popc(okm);
     any += nv;
-    if (nv & 1)  // the second half of the last pair: an all-zero primitive quartet
-      for (int i = lane; i < HFX_NCOEF; i += 32) reinterpret_cast<float*>(CF + (nv >> 1) * HFX_NCOEF + i)[1] = 0.f;
+    const int r = nv % W;
+    if (r)  // the unused components of the last packed set: all-zero primitive quartets
+      for (int i = lane; i < HFX_NCOEF * (W - r); i += 32) {
+        const int c = i / (W - r);
+        reinterpret_cast<float*>(CF + (nv / W) * HFX_NCOEF + c)[r + (i - c * (W - r))] = 0.f;
+      }
     __syncwarp();
-    const int np = (nv + 1) >> 1;
+    const int np = (nv + W - 1) / W;
     for (int j = 0; j < np; j += k) {
       for (int i = lane; i < k * nbase; i += 32) {
         const int u = i / nbase, m = i - u * nbase;
-        S[u * rsz + nacc + m] = (j + u < np) ? CF[(j + u) * HFX_NCOEF + HFX_CF_G + m] : z2;
+        S[u * rsz + nacc + m] = (j + u < np) ? CF[(j + u) * HFX_NCOEF + HFX_CF_G + m] : zv;
       }
       __syncwarp();
       uint4 e = __ldg(sched + lane);
       for (int it = 1; it <= sv.n_iter; ++it) {
         const uint4 en = __ldg(sched + it * 32 + lane);
-        sched_op<float2>(e, S, rsz, sv.zero, CF, j, np);
+        sched_op<V>(e, S, rsz, sv.zero, CF, j, np);
         __syncwarp();
         e = en;
       }
@@ -349,9 +381,7 @@ __device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const Sch
       }
       const unsigned okm = __ballot_sync(0xffffffffu, ok);
       const int pos = __popc(okm & ((1u << lane) - 1u));
-      if (ok)
-        write_set<float, 2>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps,
-                            reinterpret_cast<float*>(CF + (pos >> 1) * HFX_NCOEF) + (pos & 1));
+      if (ok) write_set<float, W>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps, slot_of(pos));
       run_sets(okm);
     }
   };
@@ -378,18 +408,33 @@ __device__ __forceinline__ int contract_g32_x2(const EriClassInfo& ci, const Sch
       const bool ok = stt == F32_OK;
       const unsigned okm = __ballot_sync(0xffffffffu, ok);
       const int pos = __popc(okm & ((1u << lane) - 1u));
-      if (ok)
-        write_set_f32<2>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps,
-                         reinterpret_cast<float*>(CF + (pos >> 1) * HFX_NCOEF) + (pos & 1));
+      if (ok) write_set_f32<W>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps, slot_of(pos));
       run_sets(okm);
     }
     if (fm[0] | fm[1] | fm[2]) fp64_sets(fm[0], fm[1], fm[2], c0);
   }
   if (!any) return 0;
-  for (int a = lane; a < nacc; a += 32) {
-    float2 sum = S[a];
-    for (int u = 1; u < k; ++u) sum = __fadd2_rn(sum, S[u * rsz + a]);
-    Sd[a] = to_f64(sum.x) + to_f64(sum.y);  // in place: read, then write
+  // the streams' sums, widened to FP64 in place: accumulator a's double overlaps the packed
+  // slot a / (W / 2), which the same or an earlier 32-wide slice reads, so each slice reads all
+  // its slots before any lane writes (the other streams' regions lie above the block)
+  for (int a0 = 0; a0 < nacc; a0 += 32) {
+    const int a = a0 + lane;
+    double w = 0.0;
+    if (a < nacc) {
+      V sum = S[a];
+      float* sf = reinterpret_cast<float*>(&sum);
+      for (int u = 1; u < k; ++u) {
+        const V v = S[u * rsz + a];
+        const float* vf = reinterpret_cast<const float*>(&v);
+#pragma unroll
+        for (int c = 0; c < W; ++c) sf[c] += vf[c];
+      }
+      w = to_f64(sf[0]);
+#pragma unroll
+      for (int c = 1; c < W; ++c) w += to_f64(sf[c]);
+    }
+    __syncwarp();
+    if (a < nacc) Sd[a] = w;
   }
   __syncwarp();
   post_stages<double>(ci, pa, bra, ket, Sd, lane);
@@ -718,7 +763,7 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const SchedVar
     const bool f32 = PREC == PREC_MIXED32;
     int ne;
     if (f32)
-      ne = contract_g32_x2(ci, sv, Ls, bra, ket, S, CF, lane);
+      ne = contract_g32_xw<HFX_FP32_PACK>(ci, sv, Ls, bra, ket, S, S + (HFX_FP32_PACK / 2) * sv.group, lane);
     else
       ne = contract_g32<double>(ci, sv, Ls, bra, ket, S, CF, lane);
     t.prim += ne;
@@ -847,7 +892,7 @@ __global__ void __launch_bounds__(64, PREC == PREC_MIXED32 ? HFX_G1F_MINB : (BAT
 template <int MODE, int PREC, bool BATCH, bool PER = false>
 __global__ void __launch_bounds__(64, BATCH ? HFX_G32B_MINB : (PREC == PREC_MIXED32 ? HFX_G32F_MINB : HFX_G32_MINB))
     eri_g32_kernel(const EriLaunch L) {
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) double smem[];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int gpb = blockDim.x >> 5;
   double* S = smem + grp * g32_stride(L.sv, PREC);
