@@ -82,8 +82,8 @@ typedef struct {
                           upper incomplete gamma functions (erfc and an upward recursion of
                           positive terms); a primitive quartet where the subtracted one exceeds
                           1/64 of the other (small T (1 - kappa)) takes the FP64 Boys step.  FP32
-                          quartets run on whole warps, two primitive quartets per float2 slot
-                          (FFMA2) */
+                          quartets run on whole warps, four primitive quartets per float4 slot
+                          (two FFMA2 per op) */
   int precision;       /* HFX_FP64 (default) or HFX_MIXED */
   int schedule;        /* HFX_SCHED_DYNAMIC (default), HFX_SCHED_QUARTET or HFX_SCHED_PAIR */
   int skip_zero_p;     /* 1 (default): skip quartets whose four density blocks P_bd, P_bc,
