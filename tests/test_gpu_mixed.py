@@ -117,3 +117,18 @@ def test_many_primitives(hfx_mod, kind, nprim):
     st = h.stats()
     assert sum(st["quartets_fp32_class"]) > 0
     assert np.abs(K - Ko).max() <= TOL and abs(e - eo) <= TOL
+
+
+def test_thread_kernel_fp32_pass(hfx_mod):
+    """The thread kernel's FP32 pass (run when a caller fixes the low classes to one quartet per
+    thread): FP32 set-up with deferred FP64 set-ups per lane, against the oracle."""
+    s, P = inputs.config1(8)
+    Ko, eo = oracle_K(s, P)
+    h = hfx_mod.HFX(s, precision=hfx_mod.HFX_MIXED).build_pairs()
+    h.set_timing(True)  # the per-class counters
+    for c in (0, 1, 2, 3, 4, 6, 7, 10, 15):
+        h.set_group_size(c, 1)
+    K = h.build_K(torch.from_numpy(P).cuda()).cpu().numpy()
+    st = h.stats()
+    assert sum(st["quartets_fp32_class"][c] for c in (0, 1, 2, 3, 4, 6, 7, 10, 15)) > 0
+    assert np.abs(K - Ko).max() <= TOL and abs(h.energy() - eo) <= TOL
