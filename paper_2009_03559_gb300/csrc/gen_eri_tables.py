@@ -680,6 +680,30 @@ def all_classes():
 STAGE_TYPE = {"hrr_bra": 0, "hrr_ket": 1, "sph": 2}
 
 
+def post_words_of(c):
+    """The post-contraction stages of a class as uint4 ops (dst | s1, s2 | s3, spherical
+    coefficient indices | direction << 12, 0), slots in the group scratch: per stage its type,
+    first op (relative) and op count, the words, and where the final block starts."""
+    T, bases = c.layout()
+    p_type, p_rel, p_n, words = [], [], [], []
+    for k, st in enumerate(c.stages):
+        src_base = bases[k]
+        dst_base = bases[k + 1]
+        p_type.append(STAGE_TYPE[st["type"]])
+        p_rel.append(len(words) // 4)
+        p_n.append(len(st["ops"]))
+        for (dst, srcs, d) in st["ops"]:
+            sl = [src_base + s for s, _ in srcs] + [0] * (3 - len(srcs))
+            cs = [cc for _, cc in srcs] + [0] * (3 - len(srcs))
+            if st["type"] != "sph":
+                cs = [0, 0, 0]
+            words.extend([((dst_base + dst) & 0xFFFF) | ((sl[0] & 0xFFFF) << 16),
+                          (sl[1] & 0xFFFF) | ((sl[2] & 0xFFFF) << 16),
+                          cs[0] | (cs[1] << 4) | (cs[2] << 8) | (d << 12),
+                          0])
+    return p_type, p_rel, p_n, words, bases[len(c.stages)]
+
+
 def emit(classes, f=sys.stdout):
     w = f.write
     w("// Generated by gen_eri_tables.py -- do not edit by hand.\n")
@@ -698,23 +722,9 @@ def emit(classes, f=sys.stdout):
                 vrr_words.extend(pack_vrr(o))
         acc_off = len(acc_words)
         acc_words.extend([(a & 0xFFFF) | ((sl & 0xFFFF) << 16) for a, sl in c.acc_src])
-        p_type, p_off, p_n = [], [], []
-        for k, st in enumerate(c.stages):
-            src_base = bases[k]
-            dst_base = bases[k + 1]
-            p_type.append(STAGE_TYPE[st["type"]])
-            p_off.append(len(post_words) // 4)
-            p_n.append(len(st["ops"]))
-            for (dst, srcs, d) in st["ops"]:
-                sl = [src_base + s for s, _ in srcs] + [0] * (3 - len(srcs))
-                cs = [cc for _, cc in srcs] + [0] * (3 - len(srcs))
-                if st["type"] != "sph":
-                    cs = [0, 0, 0]
-                post_words.extend([((dst_base + dst) & 0xFFFF) | ((sl[0] & 0xFFFF) << 16),
-                                   (sl[1] & 0xFFFF) | ((sl[2] & 0xFFFF) << 16),
-                                   cs[0] | (cs[1] << 4) | (cs[2] << 8) | (d << 12),
-                                   0])
-        out_base = bases[len(c.stages)]
+        p_type, p_rel, p_n, words, out_base = post_words_of(c)
+        p_off = [len(post_words) // 4 + r for r in p_rel]
+        post_words.extend(words)
         fl = c.flops()
         rows.append(dict(c=c, T=T, work_base=work_base, lv_off=lv_off, lv_n=lv_n, acc_off=acc_off,
                          p_type=p_type, p_off=p_off, p_n=p_n, out_base=out_base, fl=fl))
