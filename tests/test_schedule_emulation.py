@@ -13,7 +13,8 @@ primitive quartets (spherical components for d shells taken with the tables' coe
 The base values G_m come from the oracle's attenuated Boys function, the prefactor
 sqrt(2) pi^{5/4} exp(-ab/p |AB|^2) / p per pair (weight 1).  The same run with every write done
 at once (sequentially) must give the same numbers: no entry reads a slot that an entry of the
-same iteration writes."""
+same iteration writes.  The thread kernel's tables (VRR levels with folded accumulations and
+the accumulator adds) are run the same way, one primitive quartet after another."""
 import importlib.util
 import math
 import os
@@ -160,3 +161,45 @@ def test_schedules_and_post_ops_reproduce_oracle_integrals(ci):
         ref = expected(c, exps, cen, omega)
         scale = np.abs(ref).max()
         assert np.allclose(got, ref, rtol=1e-10, atol=1e-12 * scale), (c.name(), k, np.abs(got - ref).max(), scale)
+
+
+def run_levels(c, sets):
+    """The thread kernel's tables: VRR levels (packed ops, folded accumulations) and the
+    accumulator adds, one primitive quartet after another on one set of slots."""
+    S = np.zeros(c.n_acc)
+    for cf in sets:
+        V = np.zeros(c.n_vrr_slots)
+        V[:c.Lt + 1] = cf[CF["G"]:CF["G"] + c.Lt + 1]
+        nb = len(c.bra_ops)
+        for li, lvl in enumerate(c.bra_ops + c.ket_ops):
+            ket = li >= nb
+            base = KET_BASE if ket else 0
+            for o in lvl:
+                x, y, z, w = gen.pack_vrr(o)
+                dst, s1, s2, s3, s4, s5 = x & 0xFFFF, x >> 16, y & 0xFFFF, y >> 16, z & 0xFFFF, z >> 16
+                i, nA, nB, acc = w & 3, (w >> 2) & 7, (w >> 5) & 7, (w >> 8) & 1
+                v = cf[base + CF["PA"] + i] * V[s1] + (S[dst] if acc else 0.0)
+                v = cf[base + CF["WP"] + i] * V[s2] + v
+                if nA:
+                    v = cf[base + CF["CA"] + nA] * (cf[base + CF["RP"]] * V[s4] + V[s3]) + v
+                if ket and nB:
+                    v = cf[CF["CB"] + nB] * V[s5] + v
+                if acc:
+                    S[dst] = v
+                else:
+                    V[dst] = v
+        for a, sl in c.acc_src:
+            S[a] += V[sl]
+    return S
+
+
+@pytest.mark.parametrize("ci", range(len(CLASSES)), ids=[c.name() for c in CLASSES])
+def test_thread_tables_reproduce_oracle_integrals(ci):
+    c = CLASSES[ci]
+    rng = np.random.default_rng(300 + ci)
+    cen = rng.uniform(-1.5, 1.5, (4, 3))
+    exps = [rng.uniform(0.2, 3.0, 4) for _ in range(3)]
+    sets = [coef_set(e, cen, c.Lt, 0.11) for e in exps]
+    got = run_post(c, run_levels(c, sets), cen[0] - cen[1], cen[2] - cen[3])
+    ref = expected(c, exps, cen, 0.11)
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max()), c.name()
