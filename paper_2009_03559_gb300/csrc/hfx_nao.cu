@@ -15,8 +15,10 @@
 // Gaussians on the grid: for an exponent a and beta = a h^2, exp(-beta i^2) moves along one lane's
 // points (i -> i + 32) by the factor exp(-beta (64 i + 1024)), and that factor by exp(-2048 beta):
 // two exp() calls per Gaussian and lane plus the lane-independent one, then two multiplies per
-// point.  In the genetic step an individual's alpha = exp(u) and exp(-2048 beta) are made once,
-// by the lane that makes the individual, and kept with its genes.
+// point (the local search).  In the genetic step an individual's alpha = exp(u) and the factors
+// exp(-beta), exp(-64 beta), exp(-1024 beta) are made once, by the lane that makes the
+// individual, and kept with its genes; a lane's start values are then products over the lanes
+// below it (warp product scans), so evaluating an individual calls no exp().
 //
 // The paper names the two searches but does not spell them out; the readings (shared with the
 // CPU reference the tests compare against) are:
