@@ -68,9 +68,10 @@ def coef_set(ex, cen, Lt, omega):
     return cf
 
 
-def run_schedule(c, ws, sets, parallel=True):
+def run_schedule(c, ws, sets, parallel=True, dtype=np.float64):
     k, rsz = ws.k, ws.rsz
-    S = np.zeros(k * rsz)
+    S = np.zeros(k * rsz, dtype=dtype)
+    sets = [np.asarray(cf, dtype=dtype) for cf in sets]
     for u in range(k):
         S[u * rsz + c.n_acc:u * rsz + c.n_acc + c.Lt + 1] = sets[u][CF["G"]:CF["G"] + c.Lt + 1]
     words = np.array(ws.words(), dtype=np.uint64).reshape(-1, 4)
@@ -99,7 +100,7 @@ def run_schedule(c, ws, sets, parallel=True):
                 S[X + dst] = v
         for i, v in writes:
             S[i] = v
-    acc = sum(S[u * rsz:u * rsz + c.n_acc] for u in range(k))
+    acc = sum(S[u * rsz:u * rsz + c.n_acc].astype(np.float64) for u in range(k))
     return acc
 
 
@@ -203,3 +204,30 @@ def test_thread_tables_reproduce_oracle_integrals(ci):
     got = run_post(c, run_levels(c, sets), cen[0] - cen[1], cen[2] - cen[3])
     ref = expected(c, exps, cen, 0.11)
     assert np.allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max()), c.name()
+
+
+def test_fp32_recurrence_error_by_class():
+    """The schedules run in float32 on far-apart quartets (the kind that qualify for FP32),
+    horizontal recurrences in FP64: the error relative to the quartet's largest integral grows
+    with the total angular momentum, and (dd|dd) (L = 8) has the largest of all classes: the
+    class the default FP32 mask leaves in FP64."""
+    errs = {}
+    for ci, c in enumerate(CLASSES):
+        ws = gen.warp_schedules(c)[1]
+        rng = np.random.default_rng(7 + ci)
+        worst = 0.0
+        for _ in range(6):
+            A = rng.uniform(-1, 1, 3)
+            B = A + rng.uniform(-2, 2, 3)
+            shift = rng.normal(size=3)
+            shift *= rng.uniform(9, 12) / np.linalg.norm(shift)
+            Cc = shift + rng.uniform(-1, 1, 3)
+            D = Cc + rng.uniform(-2, 2, 3)
+            cf = coef_set(rng.uniform(0.1, 3.0, 4), np.array([A, B, Cc, D]), c.Lt, 0.11)
+            o64 = run_post(c, run_schedule(c, ws, [cf]), A - B, Cc - D)
+            o32 = run_post(c, run_schedule(c, ws, [cf], dtype=np.float32), A - B, Cc - D)
+            worst = max(worst, np.abs(o32 - o64).max() / np.abs(o64).max())
+        errs[c.name()] = worst
+    assert max(errs.values()) == errs["dddd"]
+    assert errs["dddd"] > 3 * max(v for k, v in errs.items() if k != "dddd")
+    assert max(errs[n] for n in ("ssss", "psss", "psps", "ppss", "ppps")) < 1e-6
