@@ -195,9 +195,9 @@ __host__ __device__ __forceinline__ int g32_stride(const SchedVariant& sv, int p
   return HFX_FP32_PACK == 4 ? 2 * sv.group + 9 * HFX_NCOEF * 2 + 2 : sv.group + 17 * HFX_NCOEF + 1;
 }
 
-template <typename R, bool PER = false>
+template <bool PER = false>
 __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedVariant& sv, const EriLaunch& L,
-                                            int bra, int ket, R* S, R* CF, int lane) {
+                                            int bra, int ket, double* S, double* CF, int lane) {
   const PairArrays pa = L.pa;
   const double omega = L.omega, omega2 = L.omega2;
   const double* boys = L.boys;
@@ -207,12 +207,11 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedV
   const int k = sv.k, rsz = sv.rsz, nacc = ci.n_acc, nbase = ci.Lt + 1;
   for (int i = lane; i < k * nacc; i += 32) {
     const int u = i / nacc;
-    S[u * rsz + (i - u * nacc)] = R(0);
+    S[u * rsz + (i - u * nacc)] = 0.0;
   }
-  if (lane < k) S[lane * rsz + sv.zero] = R(0);
-  // coefficient set 32: all zeros, for streams past the chunk's last primitive quartet (the
-  // FP32 and FP64 views of the group memory overlap, so it is laid down per quartet)
-  for (int i = lane; i < HFX_NCOEF; i += 32) CF[32 * HFX_NCOEF + i] = R(0);
+  if (lane < k) S[lane * rsz + sv.zero] = 0.0;
+  // coefficient set 32: all zeros, for streams past the chunk's last primitive quartet
+  for (int i = lane; i < HFX_NCOEF; i += 32) CF[32 * HFX_NCOEF + i] = 0.0;
   const uint4* sched = reinterpret_cast<const uint4*>(kSched) + sv.off;
   const int npq = nb * nk;
   int any = 0;
@@ -235,14 +234,14 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedV
     }
     const unsigned okm = __ballot_sync(0xffffffffu, ok);
     if (ok)
-      write_set<R>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps, CF + __popc(okm & ((1u << lane) - 1u)) * HFX_NCOEF);
+      write_set<double>(pb[ib], pk[ik], ci.E, ci.F, ci.Lt, G, ps, CF + __popc(okm & ((1u << lane) - 1u)) * HFX_NCOEF);
     const int nv = __popc(okm);
     any += nv;
     __syncwarp();
     for (int j = 0; j < nv; j += k) {
       for (int i = lane; i < k * nbase; i += 32) {
         const int u = i / nbase, m = i - u * nbase;
-        S[u * rsz + nacc + m] = (j + u < nv) ? CF[(j + u) * HFX_NCOEF + HFX_CF_G + m] : R(0);
+        S[u * rsz + nacc + m] = (j + u < nv) ? CF[(j + u) * HFX_NCOEF + HFX_CF_G + m] : 0.0;
       }
       __syncwarp();
       uint4 e = __ldg(sched + lane);
@@ -250,7 +249,7 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedV
         // the next entry is fetched before this one runs (the last fetch reads one
         // iteration past the variant's table: the tables end with a padding iteration)
         const uint4 en = __ldg(sched + it * 32 + lane);
-        sched_op<R>(e, S, rsz, sv.zero, CF, j, nv);
+        sched_op<double>(e, S, rsz, sv.zero, CF, j, nv);
         __syncwarp();
         e = en;
       }
@@ -259,26 +258,13 @@ __device__ __forceinline__ int contract_g32(const EriClassInfo& ci, const SchedV
   if (!any) return 0;
   if (k > 1) {
     for (int a = lane; a < nacc; a += 32) {
-      R sum = S[a];
+      double sum = S[a];
       for (int u = 1; u < k; ++u) sum += S[u * rsz + a];
       S[a] = sum;
     }
     __syncwarp();
   }
-  if constexpr (sizeof(R) == 4) {
-    // FP32 recurrences end at the contracted block: widen it to FP64 (through the free
-    // coefficient area) so the horizontal recurrences and the spherical step, which cancel
-    // across distant pairs, run in FP64 on the group's FP64 scratch
-    double* Sd = reinterpret_cast<double*>(S);
-    double* tmp = reinterpret_cast<double*>(CF);
-    for (int a = lane; a < nacc; a += 32) tmp[a] = to_f64(S[a]);
-    __syncwarp();
-    for (int a = lane; a < nacc; a += 32) Sd[a] = tmp[a];
-    __syncwarp();
-    post_stages<double>(ci, pa, bra, ket, Sd, lane);
-  } else {
-    post_stages<R>(ci, pa, bra, ket, S, lane);
-  }
+  post_stages<double>(ci, pa, bra, ket, S, lane);
   return any;
 }
 
@@ -765,7 +751,7 @@ __device__ __forceinline__ void g32_range(const EriClassInfo& ci, const SchedVar
     if (f32)
       ne = contract_g32_xw<HFX_FP32_PACK>(ci, sv, Ls, bra, ket, S, S + (HFX_FP32_PACK / 2) * sv.group, lane);
     else
-      ne = contract_g32<double>(ci, sv, Ls, bra, ket, S, CF, lane);
+      ne = contract_g32<false>(ci, sv, Ls, bra, ket, S, CF, lane);
     t.prim += ne;
     t.skip += npq - ne;
     if (!ne) continue;
@@ -799,7 +785,7 @@ __device__ __forceinline__ void g32_range_per(const EriClassInfo& ci, const Sche
     PerQuartet pq;
     if (!per_quartet(Ls, bra, ket, pq)) continue;
     const int npq = __ldg(Ls.pa.prim_n + bra) * __ldg(Ls.pa.prim_n + ket);
-    const int ne = contract_g32<double, true>(ci, sv, Ls, bra, ket, S, CF, lane);
+    const int ne = contract_g32<true>(ci, sv, Ls, bra, ket, S, CF, lane);
     t.prim += ne;
     t.skip += npq - ne;
     if (!ne) continue;
@@ -915,7 +901,7 @@ __global__ void __launch_bounds__(64, BATCH ? HFX_G32B_MINB : (PREC == PREC_MIXE
     for (long long t = gid; t < L.diag_n; t += ng) {
       const int p = __ldg(L.diag_list + t);
       double mx = 0.0;
-      if (contract_g32<double>(L.ci, L.sv, L, p, p, S, CF, lane)) mx = diag_max(L.ci, S + L.ci.out_base, 1);
+      if (contract_g32<false>(L.ci, L.sv, L, p, p, S, CF, lane)) mx = diag_max(L.ci, S + L.ci.out_base, 1);
       if (lane == 0) L.diag_Q[p] = sqrt(mx);
       __syncwarp();
     }
