@@ -3,6 +3,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 
 from paper_2009_03559_gb300 import inputs
 
@@ -125,3 +126,21 @@ def test_batch_of_32_matches_recipe():
             assert s.rcut == 6.0 and s.tau == 1e-8
         else:
             assert s.rcut == 0.0 and s.tau == 1e-10
+
+
+def test_nao_set_shape_confinement_normalisation():
+    """Synthetic radial functions: 2s 2p 1d per element, zero at and beyond the confining
+    radius, value and slope going to zero there, unit norm on the grid, seeded."""
+    rs = inputs.nao_set(3, seed=11)
+    assert rs.phi.shape == (15, 512)
+    assert list(rs.l) == [0, 0, 1, 1, 2] * 3
+    r = rs.h * np.arange(1, 513)
+    assert r[-1] == pytest.approx(rs.r_cut)
+    assert np.all(rs.phi[:, -1] == 0.0)
+    assert np.allclose((rs.phi ** 2 * r ** 2).sum(axis=1) * rs.h, 1.0)
+    # near r_c the function vanishes quadratically (value and slope zero at the radius)
+    tail = np.abs(rs.phi[:, -5:-1]).max(axis=1) / np.abs(rs.phi).max(axis=1)
+    assert np.all(tail < 1e-3)
+    again = inputs.nao_set(3, seed=11)
+    assert np.array_equal(again.phi, rs.phi)
+    assert not np.array_equal(inputs.nao_set(3, seed=12).phi, rs.phi)
